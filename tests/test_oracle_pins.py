@@ -1,0 +1,338 @@
+"""Pins of the CPU oracle against what the paper and the mathematics fix.
+
+Each test checks the oracle against something other than itself: a value the
+paper prints (the worked example of Section 2.1), transition rows derived by
+hand (tests/golden/hand_graph.txt), closed forms, a different algorithm for
+the same quantity (series of Eq. 3 vs. linear solve vs. Power Iteration vs.
+the sampled walk of Lemma 1), or a theorem's invariant (Lemma 3,
+Theorems 2 and 3, mass conservation).
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from golden_io import load
+from paper_2512_11606_gb300 import synth
+
+ALPHA, BETA = 0.15, 0.35
+
+
+def graph_of(fx):
+    return synth.GraphArrays(fx.n_u, fx.n_v, fx.n_a, fx.e_u, fx.e_v,
+                             np.asarray(fx.e_w, np.float32), fx.ea_u, fx.ea_a,
+                             np.asarray(fx.ea_w, np.float32))
+
+
+def frac_row(row):
+    return np.array([float(x) for x in row])
+
+
+@pytest.fixture(scope="module")
+def tiny():
+    g = synth.make_graph(**synth.TINY)
+    og = oracle.OracleGraph.from_arrays(g)
+    _, _, P = oracle.dense_matrices_of(g, BETA)
+    Pi = oracle.pi_matrix(P, ALPHA)
+    lam, _ = og.lambda_estimate(ALPHA, BETA)
+    q = int(synth.draw_queries(g.n_u, 1)[0])
+    return dict(g=g, og=og, P=P, Pi=Pi, lam=lam, q=q)
+
+
+# ----------------------------------------------------------- worked example
+
+def test_worked_example_dense_row():
+    """Example 1 (Section 2.1): P_S[u1,u2] = 3/8, P_S[u1,u3] = 1/8 (+ implied)."""
+    fx = load("worked_example.txt")
+    P_S, _, _ = oracle.dense_matrices_of(graph_of(fx), 0.0)
+    np.testing.assert_allclose(P_S[0], frac_row(fx.ps_rows[0]), rtol=0, atol=1e-15)
+
+
+@pytest.mark.parametrize("algo", ["app", "asrp"])
+def test_worked_example_one_push_round(algo):
+    """One round of Algorithm 3/4 from u1 with beta = 0 leaves r = (1-a) P_S[u1, .]."""
+    fx = load("worked_example.txt")
+    og = oracle.OracleGraph.from_arrays(graph_of(fx))
+    res = og.push(algo, ALPHA, 0.0, 0, 1e-9, lam=1.0, max_rounds=1)
+    assert res.stats["rounds"] == 1 and res.rc == 1
+    np.testing.assert_allclose(res.r_u, (1 - ALPHA) * frac_row(fx.ps_rows[0]), atol=1e-15)
+    assert res.pi[0] == pytest.approx(ALPHA, abs=1e-15)
+    assert np.all(res.pi[1:] == 0)
+
+
+# -------------------------------------------------------- hand-derived rows
+
+def test_hand_graph_dense_rows():
+    fx = load("hand_graph.txt")
+    P_S, P_A, _ = oracle.dense_matrices_of(graph_of(fx), BETA)
+    for i, row in fx.ps_rows.items():
+        np.testing.assert_allclose(P_S[i], frac_row(row), atol=1e-15)
+    for i, row in fx.pa_rows.items():
+        np.testing.assert_allclose(P_A[i], frac_row(row), atol=1e-15)
+
+
+@pytest.mark.parametrize("q", [0, 1, 2])
+@pytest.mark.parametrize("beta", [0.0, 0.25, 0.35, 1.0])
+def test_hand_graph_one_push_round(q, beta):
+    """The C oracle's two-hop push reproduces the hand rows of (1-b)P_S + b P_A."""
+    fx = load("hand_graph.txt")
+    og = oracle.OracleGraph.from_arrays(graph_of(fx))
+    res = og.push("asrp", ALPHA, beta, q, 1e-9, lam=1.0, max_rounds=1)
+    row = (1 - beta) * frac_row(fx.ps_rows[q]) + beta * frac_row(fx.pa_rows[q])
+    np.testing.assert_allclose(res.r_u, (1 - ALPHA) * row, atol=1e-15)
+
+
+def test_pins_catch_planted_mistakes():
+    """Plausible mistakes in the dense builder fail the hand pins."""
+    fx = load("hand_graph.txt")
+    g = graph_of(fx)
+    WA = np.zeros((g.n_u, g.n_a))
+    np.add.at(WA, (g.ea_u.astype(int), g.ea_a.astype(int)), g.ea_w.astype(float))
+    good = frac_row(fx.pa_rows[0])
+    # normalisers swapped (column sum on the left hop, row sum on the right)
+    swapped = (WA / WA.sum(0)[None, :]) @ (WA / WA.sum(1)[:, None]).T
+    # transposed operand (column of P_A instead of its row)
+    _, P_A, _ = oracle.dense_matrices_of(g, BETA)
+    assert not np.allclose(swapped[0], good)
+    assert not np.allclose(P_A[:, 0], good)
+    # a dropped attribute term (beta part lost) changes the pushed round
+    og = oracle.OracleGraph.from_arrays(g)
+    res = og.push("asrp", ALPHA, 0.35, 0, 1e-9, lam=1.0, max_rounds=1)
+    only_s = (1 - ALPHA) * (0.65 * frac_row(fx.ps_rows[0]))
+    assert not np.allclose(res.r_u, only_s)
+
+
+# --------------------------------------------------------------- closed forms
+
+def hub_graph(n):
+    """One V node joined to every U node, one attribute shared by all: P = J/n."""
+    u = np.arange(n, dtype=np.uint32)
+    z = np.zeros(n, dtype=np.uint32)
+    one = np.ones(n, dtype=np.float32)
+    return synth.GraphArrays(n, 1, 1, u, z, one, u, z, one)
+
+
+@pytest.mark.parametrize("n", [2, 5, 17])
+def test_closed_form_uniform_chain(n):
+    """P = J/n gives pi(u,u) = a + (1-a)/n and pi(u,j) = (1-a)/n (j != u)."""
+    g = hub_graph(n)
+    og = oracle.OracleGraph.from_arrays(g)
+    want = np.full(n, (1 - ALPHA) / n)
+    want[1] += ALPHA
+    _, _, P = oracle.dense_matrices_of(g, BETA)
+    np.testing.assert_allclose(P, np.full((n, n), 1.0 / n), atol=1e-15)
+    np.testing.assert_allclose(oracle.exact_dense(P, ALPHA, 1), want, atol=1e-14)
+    np.testing.assert_allclose(og.power_iteration(ALPHA, BETA, 1, 400), want, atol=1e-14)
+    eps = 1e-10
+    for algo in ("app", "asrp"):
+        res = og.push(algo, ALPHA, BETA, 1, eps, lam=1.0)
+        assert res.rc == 0
+        assert np.all(want - res.pi >= -1e-15) and np.all(want - res.pi <= eps * 1.0001)
+
+
+def small_random_graph(seed, n_u=8, n_v=6, n_e=18, n_a=4, m=2):
+    rng = np.random.default_rng(seed)
+    pairs = set()
+    # every node gets at least one edge
+    for u in range(n_u):
+        pairs.add((u, int(rng.integers(n_v))))
+    for v in range(n_v):
+        pairs.add((int(rng.integers(n_u)), v))
+    while len(pairs) < n_e:
+        pairs.add((int(rng.integers(n_u)), int(rng.integers(n_v))))
+    e = np.array(sorted(pairs))
+    ew = rng.uniform(0.5, 2.0, size=e.shape[0]).astype(np.float32)
+    au = np.repeat(np.arange(n_u), m)
+    aa = np.concatenate([rng.choice(n_a, size=m, replace=False) for _ in range(n_u)])
+    aw = rng.uniform(0.1, 1.0, size=au.shape[0]).astype(np.float32)
+    return synth.GraphArrays(n_u, n_v, n_a, e[:, 0].astype(np.uint32),
+                             e[:, 1].astype(np.uint32), ew, au.astype(np.uint32),
+                             aa.astype(np.uint32), aw)
+
+
+@pytest.mark.parametrize("seed", [0, 1, 2])
+def test_series_solve_and_power_iteration_agree(seed):
+    """Eq. 3 summed term by term = the linear solve = Algorithm 1."""
+    g = small_random_graph(seed)
+    _, _, P = oracle.dense_matrices_of(g, BETA)
+    np.testing.assert_allclose(P.sum(axis=1), 1.0, atol=1e-14)
+    og = oracle.OracleGraph.from_arrays(g)
+    for q in range(g.n_u):
+        ex = oracle.exact_dense(P, ALPHA, q)
+        np.testing.assert_allclose(oracle.series_sum(P, ALPHA, q, 400), ex, atol=1e-13)
+        np.testing.assert_allclose(og.power_iteration(ALPHA, BETA, q, 250), ex, atol=1e-13)
+        assert ex.sum() == pytest.approx(1.0, abs=1e-13)
+
+
+def test_monte_carlo_walks_match_exact():
+    """Lemma 1: the stop distribution of the sampled walk is pi(q, .)."""
+    g = small_random_graph(5)
+    _, _, P = oracle.dense_matrices_of(g, BETA)
+    q, n = 3, 2_000_000
+    emp = oracle.monte_carlo_walks(g, ALPHA, BETA, q, n)
+    ex = oracle.exact_dense(P, ALPHA, q)
+    sigma = np.sqrt(ex * (1 - ex) / n)
+    assert np.all(np.abs(emp - ex) <= 5 * sigma + 1e-6), (emp, ex)
+
+
+def test_beta_selects_terms():
+    """beta = 0 ignores attribute weights; beta = 1 ignores edge weights."""
+    g = small_random_graph(3)
+    g2 = synth.GraphArrays(g.n_u, g.n_v, g.n_a, g.e_u, g.e_v, g.e_w, g.ea_u, g.ea_a,
+                           (g.ea_w * np.linspace(0.3, 3.0, g.ea_w.shape[0])).astype(np.float32))
+    g3 = synth.GraphArrays(g.n_u, g.n_v, g.n_a, g.e_u, g.e_v,
+                           (g.e_w * np.linspace(0.3, 3.0, g.e_w.shape[0])).astype(np.float32),
+                           g.ea_u, g.ea_a, g.ea_w)
+    a, b, c = (oracle.OracleGraph.from_arrays(x) for x in (g, g2, g3))
+    np.testing.assert_allclose(a.power_iteration(ALPHA, 0.0, 2, 200),
+                               b.power_iteration(ALPHA, 0.0, 2, 200), atol=1e-15)
+    np.testing.assert_allclose(a.power_iteration(ALPHA, 1.0, 2, 200),
+                               c.power_iteration(ALPHA, 1.0, 2, 200), atol=1e-15)
+    assert not np.allclose(a.power_iteration(ALPHA, BETA, 2, 200),
+                           b.power_iteration(ALPHA, BETA, 2, 200))
+
+
+def test_disconnected_components_have_zero_cross_scores():
+    g1 = small_random_graph(7, n_u=5, n_v=4, n_e=9, n_a=3, m=1)
+    g2 = small_random_graph(8, n_u=4, n_v=3, n_e=7, n_a=2, m=1)
+    g = synth.GraphArrays(
+        9, 7, 5,
+        np.concatenate([g1.e_u, g2.e_u + 5]).astype(np.uint32),
+        np.concatenate([g1.e_v, g2.e_v + 4]).astype(np.uint32),
+        np.concatenate([g1.e_w, g2.e_w]),
+        np.concatenate([g1.ea_u, g2.ea_u + 5]).astype(np.uint32),
+        np.concatenate([g1.ea_a, g2.ea_a + 3]).astype(np.uint32),
+        np.concatenate([g1.ea_w, g2.ea_w]))
+    og = oracle.OracleGraph.from_arrays(g)
+    _, _, P = oracle.dense_matrices_of(g, BETA)
+    ex = oracle.exact_dense(P, ALPHA, 1)
+    assert np.all(ex[5:] == 0)
+    res = og.push("asrp", ALPHA, BETA, 1, 1e-9, lam=1.0)
+    assert np.all(res.pi[5:] == 0) and np.all(res.r_u[5:] == 0)
+
+
+def test_duplicate_pairs_are_merged():
+    g = small_random_graph(4)
+    dup = synth.GraphArrays(g.n_u, g.n_v, g.n_a,
+                            np.concatenate([g.e_u, g.e_u[:3]]),
+                            np.concatenate([g.e_v, g.e_v[:3]]),
+                            np.concatenate([g.e_w, g.e_w[:3]]),
+                            g.ea_u, g.ea_a, g.ea_w)
+    merged_w = g.e_w.copy()
+    merged_w[:3] *= 2
+    single = synth.GraphArrays(g.n_u, g.n_v, g.n_a, g.e_u, g.e_v, merged_w,
+                               g.ea_u, g.ea_a, g.ea_w)
+    a, b = oracle.OracleGraph.from_arrays(dup), oracle.OracleGraph.from_arrays(single)
+    assert a.n_e == g.n_e
+    np.testing.assert_allclose(a.power_iteration(ALPHA, BETA, 0, 100),
+                               b.power_iteration(ALPHA, BETA, 0, 100), atol=1e-15)
+
+
+def test_invalid_inputs_raise():
+    g = small_random_graph(1)
+    bad = synth.GraphArrays(g.n_u, g.n_v, g.n_a, g.e_u, g.e_v, -g.e_w, g.ea_u, g.ea_a, g.ea_w)
+    with pytest.raises(ValueError):
+        oracle.OracleGraph.from_arrays(bad)
+    og = oracle.OracleGraph.from_arrays(g)
+    with pytest.raises(ValueError):
+        og.push("asrp", ALPHA, BETA, g.n_u, 1e-6, lam=1.0)
+    with pytest.raises(ValueError):
+        og.push("asrp", ALPHA, BETA, 0, 0.0, lam=1.0)
+
+
+def test_dangling_rows_leak_and_conserve():
+    """A U node without attributes drops the beta share (reading of Eq. 2)."""
+    g = small_random_graph(9)
+    keep = g.ea_u != 2
+    g2 = synth.GraphArrays(g.n_u, g.n_v, g.n_a, g.e_u, g.e_v, g.e_w,
+                           g.ea_u[keep], g.ea_a[keep], g.ea_w[keep])
+    og = oracle.OracleGraph.from_arrays(g2)
+    res = og.push("asrp", ALPHA, BETA, 2, 1e-10, lam=1.0)
+    s = res.stats
+    assert s["leak"] > 0
+    assert s["reserve_sum"] + s["resid_sum"] + s["leak"] == pytest.approx(1.0, abs=1e-12)
+    _, _, P = oracle.dense_matrices_of(g2, BETA)
+    assert P[2].sum() == pytest.approx(1 - BETA, abs=1e-15)
+    ex = oracle.exact_dense(P, ALPHA, 2)
+    assert np.all(ex - res.pi >= -1e-15) and np.all(ex - res.pi <= 1e-10)
+
+
+# ------------------------------------------------ theorems on the tiny graph
+
+def test_tiny_no_dangling_and_row_stochastic(tiny):
+    np.testing.assert_allclose(tiny["P"].sum(axis=1), 1.0, atol=1e-12)
+
+
+def test_lambda_bounds_column_sums(tiny):
+    """Theorem 3: lambda >= max_i sum_j pi(u_j, u_i)."""
+    colsum = tiny["Pi"].sum(axis=0).max()
+    assert tiny["lam"] >= colsum
+    # the bound is tight up to the tail term |U| (1-alpha)^T <= 0.01
+    assert tiny["lam"] <= colsum + 0.0101
+
+
+def test_lemma3_invariant_every_round(tiny):
+    """Lemma 3: pi(q, .) = pi_hat + r Pi after every round (APP and ASRP)."""
+    og, Pi, q, lam = tiny["og"], tiny["Pi"], tiny["q"], tiny["lam"]
+    exact = Pi[q]
+    for algo in ("asrp", "app"):
+        full = og.push(algo, ALPHA, BETA, q, 1e-6, lam=lam)
+        R = full.stats["rounds"]
+        for k in sorted({1, 2, 3, 5, R // 2, R}):
+            res = og.push(algo, ALPHA, BETA, q, 1e-6, lam=lam, max_rounds=k)
+            np.testing.assert_allclose(res.pi + res.r_u @ Pi, exact, atol=1e-12)
+            assert np.all(res.pi >= 0) and np.all(res.r_u >= 0)
+
+
+@pytest.mark.parametrize("eps", [1e-4, 1e-6, 1e-8])
+def test_theorem2_error_bound(tiny, eps):
+    """Theorem 2: 0 <= pi - pi_hat <= eps with the certified lambda; APP too."""
+    og, Pi, q, lam = tiny["og"], tiny["Pi"], tiny["q"], tiny["lam"]
+    exact = Pi[q]
+    for algo in ("asrp", "app"):
+        res = og.push(algo, ALPHA, BETA, q, eps, lam=lam)
+        assert res.rc == 0
+        err = exact - res.pi
+        assert err.min() >= -1e-14 and err.max() <= eps, (algo, err.min(), err.max())
+    fp = og.forward_push(ALPHA, BETA, q, eps)
+    err = exact - fp.pi
+    assert err.min() >= -1e-14 and err.max() <= eps
+
+
+def test_mass_conservation_per_round(tiny):
+    og, q, lam = tiny["og"], tiny["q"], tiny["lam"]
+    res = og.push("asrp", ALPHA, BETA, q, 1e-6, lam=lam)
+    t = res.trace
+    np.testing.assert_allclose(t["sum_pi"] + t["sum_r"], 1.0, atol=1e-12)
+    assert np.all(np.diff(t["sum_pi"]) >= 0)
+    assert np.all(np.diff(t["n_p"].astype(np.int64)) > 0)
+
+
+def test_asrp_switch_and_termination_consistency(tiny):
+    """Rounds after the switch are synchronous; the loop ends at max r <= eps_f."""
+    og, q, lam = tiny["og"], tiny["q"], tiny["lam"]
+    eps = 1e-6
+    res = og.push("asrp", ALPHA, BETA, q, eps, lam=lam)
+    s, t = res.stats, res.trace
+    assert s["max_resid"] <= eps / lam
+    assert np.all(t["max_r"][:-1] > eps / lam)
+    if s["switch_round"]:
+        sr = s["switch_round"]
+        assert np.all(t["phase"][: sr - 1] == 0) and np.all(t["phase"][sr - 1:] == 1)
+        # the budget test that fired: n_p >= 2(|E|+|E_A|) log_{1/(1-a)}(M/eps_f)
+        EE = og.n_e + og.n_ea
+        M = t["max_r"][sr - 2]
+        budget = 2 * EE * max(0.0, math.log(M / (eps / lam)) / math.log(1 / (1 - ALPHA)))
+        assert t["n_p"][sr - 2] >= budget
+    never = og.push("asrp", ALPHA, BETA, q, eps, lam=lam, switch_rule=2)
+    assert never.stats["switch_round"] == 0
+    np.testing.assert_allclose(never.pi, res.pi, atol=eps)
+
+
+def test_topk_matches_sorting(tiny):
+    rng = np.random.default_rng(3)
+    s = np.round(rng.random(500), 2)            # many ties
+    nodes, vals = oracle.topk(s, 50)
+    order = np.lexsort((np.arange(500), -s))[:50]
+    assert np.array_equal(nodes, order) and np.array_equal(vals, s[order])
