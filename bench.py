@@ -1,0 +1,450 @@
+#!/usr/bin/env python
+"""AHPP query throughput on one GB300 (or N, one process per GPU).
+
+Workload (default): the medium synthetic attributed bipartite graph
+(|U| = 1M, |V| = 500k, |E| = 20M Zipf(2.1) degrees, uniform(0.5,1.5) FP32
+edge weights; |A| = 10k attributes, 20 per node, lognormal weights,
+row-normalised, stored as bfloat16), ASRP with the Theorem 3 lambda,
+eps = 1e-6, top-100.  One step = one batch of 1,024 queries drawn uniformly
+from U, pushed by the batched persistent launch (graph and query arrays
+resident in HBM).  The plain one-query-at-a-time GPU push is timed on the
+same graph as the comparison point, and the FP64 CPU oracle on the host
+cores as the CPU baseline.
+
+Prints one JSON line (rank 0).  `--impl reference` times the CPU oracle
+instead (the reference arm; this paper has no reference code).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import multiprocessing as mp
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_2512_11606_gb300 import synth  # noqa: E402  (input recipe only)
+
+ALPHA, BETA = 0.15, 0.35
+METRIC = "AHPP queries/sec at eps=1e-6 (batched persistent push)"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--batch", type=int, default=1024)
+    ap.add_argument("--eps", type=float, default=1e-6)
+    ap.add_argument("--k", type=int, default=100)
+    ap.add_argument("--plain-queries", type=int, default=6)
+    ap.add_argument("--cpu-queries", type=int, default=0, help="0: one per host core (max 16)")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--graph", default="medium", choices=["medium", "tiny"])
+    return ap.parse_args()
+
+
+def graph_spec(name):
+    return dict(synth.MEDIUM_BF16) if name == "medium" else dict(synth.TINY, bf16=True)
+
+
+def workload_config(args, extra=None):
+    spec = graph_spec(args.graph)
+    cfg = {
+        "workload": (f"{args.graph} attributed bipartite graph |U|={spec['n_u']:,} |V|={spec['n_v']:,} "
+                     f"|E|={spec['n_e']:,} Zipf({spec['gamma_u']}) degrees, |A|={spec['n_a']:,} "
+                     f"x{spec['m']} bf16 attribute weights; ASRP (Theorem 3 lambda), "
+                     f"alpha={ALPHA}, beta={BETA}, eps={args.eps:g}, top-{args.k}; "
+                     f"{args.batch} queries per step (batched persistent launch)"),
+        "graph": args.graph,
+        "batch_queries_per_gpu": args.batch,
+        "eps": args.eps,
+        "k": args.k,
+        "l2": "inputs larger than L2 (graph ~0.7 GB + per-tile state ~0.45 GB per round)",
+        "parallelism": f"replicas{args.gpus}" if args.gpus > 1 else "1 GPU",
+    }
+    if extra:
+        cfg.update(extra)
+    return cfg
+
+
+# ------------------------------------------------------------------- oracle
+
+_OG = None
+
+
+def _oracle_worker(args):
+    q, eps, lam = args
+    t0 = time.perf_counter()
+    res = _OG.push("asrp", ALPHA, BETA, int(q), eps, lam=lam)
+    return time.perf_counter() - t0, res.stats["rounds"]
+
+
+def cpu_oracle_sample(g, eps, n_queries, seed=11):
+    """Time the FP64 oracle (as it stands) on a bounded sample of queries,
+    one query per process (fork before any CUDA use)."""
+    import oracle
+    global _OG
+    t0 = time.perf_counter()
+    _OG = oracle.OracleGraph.from_arrays(g)
+    lam, _ = _OG.lambda_estimate(ALPHA, BETA)
+    prep = time.perf_counter() - t0
+    qs = synth.draw_queries(g.n_u, n_queries, seed=seed)
+    ctx = mp.get_context("fork")
+    t1 = time.perf_counter()
+    with ctx.Pool(n_queries) as pool:
+        out = pool.map(_oracle_worker, [(int(q), eps, lam) for q in qs])
+    wall = time.perf_counter() - t1
+    lat = [o[0] for o in out]
+    return {
+        "value": n_queries / wall,
+        "unit": "queries/s",
+        "cores": n_queries,
+        "kind": "oracle",
+        "sample": (f"{n_queries} ASRP queries (FP64, single-threaded each, one process per core) "
+                   f"on the same graph; wall {wall:.1f} s; per-query p50 "
+                   f"{statistics.median(lat) * 1e3:.0f} ms; oracle lambda {lam:.2f} computed in "
+                   f"{prep:.1f} s preprocessing (not timed)"),
+        "lambda": lam,
+        "p50_ms": statistics.median(lat) * 1e3,
+        "p99_ms": float(np.percentile(lat, 99)) * 1e3,
+    }
+
+
+def host_cores():
+    try:
+        return len(os.sched_getaffinity(0))
+    except Exception:
+        return os.cpu_count() or 1
+
+
+# ------------------------------------------------------------------- clocks
+
+class ClockSampler:
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            threading.Thread(target=self._read, daemon=True).start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                mx.append(float(parts[1]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[4:8]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def gpu_index(local_rank):
+    vis = os.environ.get("CUDA_VISIBLE_DEVICES")
+    if vis:
+        ids = [x.strip() for x in vis.split(",") if x.strip()]
+        if local_rank < len(ids) and ids[local_rank].isdigit():
+            return int(ids[local_rank])
+    return local_rank
+
+
+def measured_peak():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+# ------------------------------------------------------------ byte model
+
+def round_bytes(info, lanes, bf16=True):
+    """Algorithmic DRAM bytes of one pull round of a tile with `lanes` queries.
+
+    Graph (once per round, shared by the lanes): phase 1 streams V->U
+    (index + coefficient, 8 B/edge) and A->U (index + weight, 6 B with bf16);
+    phase 2 streams U->V (8 B/edge) and U->A (6 B); row offsets of the four
+    directions.  State (per lane): phase 1 reads r_U once and writes t_V and
+    t_A; phase 2 reads t_V and t_A once, reads and writes r_U, and
+    read-modify-writes the reserve and its Kahan compensation.
+    """
+    wa = 2 if bf16 else 4
+    nU, nV, nA, nE, nEA = (info[k] for k in ("n_u", "n_v", "n_a", "n_e", "n_ea"))
+    graph = 2 * (4 + 4) * nE + 2 * (4 + wa) * nEA + 4 * (2 * nU + nV + nA + 4) + 4 * nU
+    state = lanes * 4 * (nU + nV + nA + nV + nA + 2 * nU + 4 * nU)
+    return graph + state
+
+
+def topk_bytes(info, queries):
+    return queries * 4 * info["n_u"]
+
+
+# ------------------------------------------------------------------ ours
+
+def run_ours(args, rank, world, local_rank):
+    import torch
+    from paper_2512_11606_gb300 import ahpp
+
+    spec = graph_spec(args.graph)
+    g = synth.make_graph(**spec)
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        n = args.cpu_queries or min(16, host_cores())
+        cpu = cpu_oracle_sample(g, args.eps, n)
+
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    G = ahpp.Graph.from_arrays(g, device=local_rank)
+    info = G.info
+    stream = torch.cuda.Stream(device=dev)
+    B, K, W = args.batch, args.steps, args.warmup
+    qs_all = synth.draw_queries(g.n_u, B * (W + K), seed=11 + 1000 * rank).reshape(W + K, B)
+    q_t = [torch.from_numpy(qs_all[i].astype(np.int32)).to(dev) for i in range(W + K)]
+    eps_t = torch.full((B,), args.eps, dtype=torch.float64, device=dev)
+    k_t = torch.full((B,), args.k, dtype=torch.int32, device=dev)
+    nodes_t = torch.empty((B, args.k), dtype=torch.int32, device=dev)
+    scores_t = torch.empty((B, args.k), dtype=torch.float32, device=dev)
+    n_t = torch.empty((B,), dtype=torch.int32, device=dev)
+    stats_t = torch.empty((B, ahpp.STATS_BYTES), dtype=torch.uint8, device=dev)
+    torch.cuda.synchronize()
+
+    def step(i):
+        G.query_batch_device(q_t[i], eps_t, k_t, args.k, nodes_t, scores_t, n_t, stats_t, stream)
+
+    for i in range(W):
+        step(i)
+    stream.synchronize()
+
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    clk = ClockSampler(gpu_index(local_rank))
+    clk.start()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(K)]
+    all_stats = []
+    t0 = time.perf_counter()
+    for j in range(K):
+        with torch.cuda.stream(stream):
+            ev[j][0].record(stream)
+        step(W + j)
+        with torch.cuda.stream(stream):
+            ev[j][1].record(stream)
+    stream.synchronize()
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - t0
+    if world > 1:
+        torch.distributed.barrier()
+    clocks = clk.stop()
+    launch_ms = [a.elapsed_time(b) for a, b in ev]
+    dev_s = sum(launch_ms) / 1e3
+    st = stats_t.cpu().numpy().view(np.uint8)
+    stats = np.frombuffer(st.tobytes(), dtype=np.dtype([
+        ("rounds", "u4"), ("switch_round", "u4"), ("dense_rounds", "u4"), ("status", "u4"),
+        ("pushes", "u8"), ("n_p", "u8"), ("resid_sum", "f8"), ("reserve_sum", "f8"),
+        ("mass_err", "f8"), ("max_resid", "f8"), ("lambda", "f8"), ("eps_f", "f8")]))
+    rounds = stats["rounds"].astype(np.int64)
+    tile = 32
+    tile_rounds = int(sum(rounds[i:i + tile].max() for i in range(0, B, tile)))
+
+    # max over ranks
+    t_max = dev_s
+    if world > 1:
+        t = torch.tensor([dev_s], dtype=torch.float64, device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        t_max = float(t.item())
+    value = world * B * K / t_max
+
+    # e2e through the host API (pinned-free host numpy buffers, copies inside)
+    e2e = None
+    if not args.no_e2e:
+        host_q = [qs_all[W + j] for j in range(K)]
+        G.query_batch(host_q[0][:64], args.eps, args.k)       # warm the host path
+        torch.cuda.synchronize()
+        te = time.perf_counter()
+        for j in range(K):
+            G.query_batch(host_q[j], args.eps, args.k)
+        te = time.perf_counter() - te
+        if world > 1:
+            t = torch.tensor([te], dtype=torch.float64, device=dev)
+            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+            te = float(t.item())
+        e2e = {"value": world * B * K / te, "unit": "queries/s",
+               "h2d_bytes_per_step": B * (4 + 8 + 4),
+               "d2h_bytes_per_step": B * (args.k * 8 + 4 + ahpp.STATS_BYTES)}
+
+    # plain one-query-at-a-time GPU push on the same graph
+    plain = None
+    if rank == 0 and args.plain_queries > 0:
+        pq = synth.draw_queries(g.n_u, args.plain_queries + 1, seed=77)
+        pn = torch.empty(args.k, dtype=torch.int32, device=dev)
+        ps = torch.empty(args.k, dtype=torch.float32, device=dev)
+        pc = torch.empty(1, dtype=torch.int32, device=dev)
+        G.query_device(int(pq[0]), args.eps, args.k, pn, ps, pc, None, stream)
+        stream.synchronize()
+        lat = []
+        for q in pq[1:]:
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            with torch.cuda.stream(stream):
+                a.record(stream)
+            G.query_device(int(q), args.eps, args.k, pn, ps, pc, None, stream)
+            with torch.cuda.stream(stream):
+                b.record(stream)
+            stream.synchronize()
+            lat.append(a.elapsed_time(b))
+        plain = {"qps": 1e3 / statistics.mean(lat), "p50_ms": statistics.median(lat),
+                 "p99_ms": float(np.percentile(lat, 99)), "queries": len(lat),
+                 "rounds_example": int(G.query(int(pq[1]), args.eps, 1).stats["rounds"])}
+
+    # roofline of the dominant kernel (the batched persistent launch)
+    peak, peak_kind = measured_peak()
+    alg = tile_rounds * round_bytes(info, tile) + topk_bytes(info, B)   # one launch (last step)
+    achieved = alg / (sum(launch_ms) / K / 1e3) / 1e9
+    roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+            "frac": achieved / peak, "traffic": None,
+            "peak_source": f"{peak_kind} hbm_gbs (MEASURED_PEAKS.json)",
+            "kernel": "k_batch (persistent, all rounds + top-k of one 1,024-query step)",
+            "algorithmic_bytes_per_launch": alg,
+            "tile_rounds_per_launch": tile_rounds}
+
+    lat_ms = launch_ms
+    out = {
+        "metric": METRIC,
+        "value": value,
+        "unit": "queries/s",
+        "n_gpus": world,
+        "steps": K,
+        "warmup": W,
+        "ms_per_step": 1e3 * t_max / K,
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f32",
+        "data": "synthetic (seeded Philox power-law graph; the paper's datasets are not available)",
+        "config": workload_config(args, {"lambda": info["lambda"], "batch_groups": info["batch_groups"],
+                                         "tile": info["batch_tile"]}),
+        "p50_ms": statistics.median(lat_ms),
+        "p99_ms": float(np.percentile(lat_ms, 99)),
+        "latency_note": "batched: a query completes with its 1,024-query step",
+        "plain": plain,
+        "speedup_vs_plain": (value / world / plain["qps"]) if plain else None,
+        "rounds_mean": float(rounds.mean()),
+        "rounds_max": int(rounds.max()),
+        "not_converged": int((stats["status"] != 0).sum()),
+        "mass_err_max": float(stats["mass_err"].max()),
+        "roofline": roof,
+        "cpu_baseline": cpu and {k: cpu[k] for k in ("value", "unit", "cores", "kind", "sample")},
+        "e2e": e2e,
+        "gpu_launches": K,
+        "clocks": clocks,
+        "wall_s": wall,
+    }
+    G.close()
+    return out
+
+
+def run_reference(args, rank, world):
+    """The reference arm: the FP64 CPU oracle on the host cores."""
+    if rank != 0:
+        return None
+    spec = graph_spec(args.graph)
+    g = synth.make_graph(**spec)
+    n = args.cpu_queries or min(16, host_cores())
+    import oracle
+    global _OG
+    _OG = oracle.OracleGraph.from_arrays(g)
+    lam, _ = _OG.lambda_estimate(ALPHA, BETA)
+    ctx = mp.get_context("fork")
+    for i in range(args.warmup):
+        pass  # the oracle has no warm-up state; warm-up steps are no-ops
+    times = []
+    done = 0
+    qs = synth.draw_queries(g.n_u, n * max(args.steps, 1), seed=11).reshape(max(args.steps, 1), n)
+    with ctx.Pool(n) as pool:
+        for j in range(args.steps):
+            t0 = time.perf_counter()
+            pool.map(_oracle_worker, [(int(q), args.eps, lam) for q in qs[j]])
+            times.append(time.perf_counter() - t0)
+            done += n
+    total = sum(times)
+    value = done / total
+    return {
+        "metric": METRIC, "value": value, "unit": "queries/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "impl": "reference",
+        "config": workload_config(args, {"reference": "FP64 CPU oracle (the paper ships no code)"}),
+        "cpu_baseline": {"value": value, "unit": "queries/s", "cores": n, "kind": "oracle",
+                         "sample": f"{n} queries per step, one process per core, lambda {lam:.2f}"},
+        "e2e": {"value": value, "unit": "queries/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+
+
+def main():
+    args = parse()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        out = run_reference(args, rank, world)
+        if out is not None:
+            print(json.dumps(out), flush=True)
+        return
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        torch.cuda.set_device(local_rank)
+        dist.init_process_group("nccl")
+    out = run_ours(args, rank, world, local_rank)
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,69 @@
+// Batched multi-source push: state and launch parameters.
+//
+// A tile holds kTile queries; every per-node state array of a tile is laid
+// out [node][kTile] (query-minor), so a warp that visits one neighbour reads
+// or writes the 32 queries' values of that neighbour as one 128-byte line.
+// The graph is streamed once per round per tile, shared by all its queries.
+// `groups` tiles run concurrently, each on its own slice of the persistent
+// grid with its own barrier; a group walks its tiles one after another.
+#pragma once
+#include "../../include/ahpp.h"
+#include "ahpp_internal.cuh"
+
+namespace ahpp {
+
+constexpr int kTile = 32;          // queries per tile (one per lane)
+constexpr int kRadixBits = 8;      // top-k digit width (per-lane histograms of 256 bins)
+constexpr int kRadixBins = 1 << kRadixBits;
+constexpr int kRadixPasses = 64 / kRadixBits;
+
+// Buffers of one concurrent group (one tile in flight).
+struct TileBuf {
+  float *r_u = nullptr, *pi = nullptr, *pic = nullptr;   // [n_u][kTile]
+  float *t_v = nullptr, *t_a = nullptr;                  // [n_v][kTile], [n_a][kTile]
+  float* split_acc = nullptr;                            // [n_split][kTile]
+  uint32_t* split_cnt = nullptr;                         // [n_split]
+  RAcc* racc = nullptr;                                  // [5][kTile]: 3 rounds + 2 final sums
+  GridBarrier* bar = nullptr;
+  unsigned int* hist = nullptr;                          // [kRadixPasses][kTile][kRadixBins]
+  unsigned long long* cand = nullptr;                    // [kTile][kmax] selected keys
+  uint32_t* cand_cnt = nullptr;                          // [kTile]
+};
+
+constexpr int kMaxGroups = 8;
+
+struct BatchState {
+  TileBuf tb[kMaxGroups];
+  uint32_t n_groups = 0;       // buffers allocated
+  uint32_t kmax_cap = 0;       // candidate capacity per lane
+};
+
+struct BatchParams {
+  uint32_t n = 0;                          // queries
+  const uint32_t* q = nullptr;             // caller ids (device)
+  const double* eps = nullptr;             // (device)
+  const uint32_t* k = nullptr;             // (device), may be null when kmax == 0
+  uint32_t kmax = 0;                       // output stride per query
+  uint32_t* out_nodes = nullptr;           // [n][kmax] caller ids
+  float* out_scores = nullptr;             // [n][kmax]
+  uint32_t* out_n = nullptr;               // [n]
+  ahpp_stats* out_stats = nullptr;         // [n], nullable
+  float* out_dense = nullptr;              // [n][n_u] caller order, nullable
+  const uint32_t* u_old2new = nullptr;
+  const uint32_t* u_new2old = nullptr;
+  int algo = 2;
+  int kahan = 1;
+  int switch_rule = 0;
+  double lambda = 1.0;
+  double log_inv = 0.0;
+  uint32_t e_tot = 0;
+  uint32_t max_rounds = 0;
+  uint32_t groups = 1;
+  uint32_t dense_div = 32;
+};
+
+int launch_batch(const DevGraph& g, const BatchState& s, const BatchParams& p, bool bf16,
+                 int grid, cudaStream_t stream);
+int batch_max_grid(bool bf16, int sm_count);
+
+}  // namespace ahpp

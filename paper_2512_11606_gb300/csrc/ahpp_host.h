@@ -1,0 +1,105 @@
+// Host-side definitions shared by the library's translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <atomic>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "../../include/ahpp.h"
+#include "ahpp_internal.cuh"
+#include "ahpp_query1.cuh"
+#include "ahpp_batch.cuh"
+
+namespace ahpp {
+
+void set_error(const std::string& msg);
+int cuda_fail(cudaError_t e, const char* where);
+
+#define AHPP_CUDA(call)                                   \
+  do {                                                    \
+    cudaError_t e_ = (call);                              \
+    if (e_ != cudaSuccess) return ::ahpp::cuda_fail(e_, #call); \
+  } while (0)
+
+// Host copy of one adjacency direction before upload.
+struct HostAdj {
+  std::vector<uint32_t> off, idx;
+  std::vector<float> w;        // raw weights
+  std::vector<float> c;        // direction coefficient (structure only)
+};
+
+struct HostItems {
+  std::vector<uint4> items;
+  std::vector<uint32_t> split_nchunks;
+};
+
+// Work-item shapes.
+struct ItemShape {
+  uint32_t short_max;   // rows with at most this many neighbours are "short"
+  uint32_t group_rows;  // short rows per item (single query: one per lane)
+  uint32_t group_nnz;   // max neighbours per short item (batched)
+  uint32_t chunk;       // neighbours per chunk of a long row
+};
+
+HostItems build_items(const std::vector<uint32_t>& deg, const ItemShape& shape);
+
+// Device allocation tracked by the graph.
+struct DevBuf {
+  void* p = nullptr;
+  size_t bytes = 0;
+};
+
+}  // namespace ahpp
+
+struct ahpp_graph {
+  ahpp_config cfg{};
+  int device = 0;
+  int sm_count = 0;
+  cudaStream_t stream = nullptr;
+  std::mutex mu;
+
+  uint64_t n_u = 0, n_v = 0, n_a = 0, n_e = 0, n_ea = 0;
+  double lambda = 1.0;
+  uint32_t lambda_T = 0;
+  bool bf16 = true;
+
+  ahpp::DevGraph dg{};
+  std::vector<ahpp::DevBuf> bufs;   // everything allocated for the graph
+  uint64_t graph_bytes = 0;
+
+  // internal <-> caller id maps of U
+  std::vector<uint32_t> h_u_old2new, h_u_new2old;
+  uint32_t* d_u_new2old = nullptr;
+  uint32_t* d_u_old2new = nullptr;
+
+  // single-query state
+  ahpp::Q1State q1{};
+  int q1_grid = 0;
+  uint32_t n_split1 = 0;
+  uint64_t q1_bytes = 0;
+
+  // batched state (allocated on first use, grown on demand)
+  ahpp::BatchState bt{};
+  uint32_t batch_tile = 32, batch_groups = 1;
+  int bt_grid = 0;
+  uint64_t tile_bytes = 0;
+
+  // top-k scratch
+  void* topk_scratch = nullptr;
+  size_t topk_scratch_bytes = 0;
+
+  void* alloc(size_t bytes);          // cudaMalloc + track (nullptr on failure)
+  void release_all();
+};
+
+namespace ahpp {
+int build_graph(const ahpp_graph_desc* desc, ahpp_graph* g);
+int run_lambda(ahpp_graph* g);
+int run_query1(ahpp_graph* g, uint32_t q_new, double eps, uint32_t lambda_T_mode,
+               cudaStream_t stream, QCtl* h_ctl);
+int topk_single(ahpp_graph* g, const float* d_score, uint32_t k, uint32_t* d_nodes,
+                float* d_scores, uint32_t* d_n, cudaStream_t stream);
+}  // namespace ahpp
