@@ -287,7 +287,7 @@ def run_ours(args, rank, world, local_rank):
         ("pushes", "u8"), ("n_p", "u8"), ("resid_sum", "f8"), ("reserve_sum", "f8"),
         ("mass_err", "f8"), ("max_resid", "f8"), ("lambda", "f8"), ("eps_f", "f8")]))
     rounds = stats["rounds"].astype(np.int64)
-    tile = 32
+    tile = int(info["batch_tile"])
     tile_rounds = int(sum(rounds[i:i + tile].max() for i in range(0, B, tile)))
 
     # max over ranks

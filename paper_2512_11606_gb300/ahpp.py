@@ -13,7 +13,7 @@ from dataclasses import dataclass
 import numpy as np
 
 HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(HERE, "_build", "libahpp_gb300.so")
+LIB_PATH = os.environ.get("AHPP_LIB") or os.path.join(HERE, "_build", "libahpp_gb300.so")
 
 AHPP_OK, AHPP_EINVAL, AHPP_ENOMEM, AHPP_ECUDA = 0, -1, -2, -3
 AHPP_ENOTCONVERGED, AHPP_EBUSY, AHPP_ETIMEOUT, AHPP_ESTATE = -4, -5, -6, -7

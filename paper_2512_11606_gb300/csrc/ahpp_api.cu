@@ -320,7 +320,7 @@ int ahpp_load_graph(const ahpp_graph_desc* desc, const ahpp_config* cfg, ahpp_gr
   ahpp_graph* g = new ahpp_graph();
   g->cfg = c;
   g->device = c.device;
-  g->batch_tile = 32;
+  g->batch_tile = ahpp::kTile;
   g->batch_groups = c.batch_groups ? c.batch_groups : 1;
   int rc = AHPP_OK;
   if (cudaDeviceGetAttribute(&g->sm_count, cudaDevAttrMultiProcessorCount, c.device) != cudaSuccess ||

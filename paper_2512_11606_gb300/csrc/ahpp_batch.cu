@@ -46,210 +46,374 @@ __device__ __forceinline__ void flush_lane_partials(Partials& p, RAcc* acc) {
       np += s_np[w][lane]; sm += s_sum[w][lane];
     }
     RAcc* a = &acc[lane];
-    if (m > 0.f) atomicMax(&a->max_r_bits, __float_as_uint(m));
-    if (mk) atomicAdd(&a->marked, mk);
-    if (dg) atomicAdd(&a->marked_deg, dg);
-    if (np) atomicAdd(&a->np_flush, np);
-    if (sm != 0.0) atomicAdd(&a->sum_r, sm);
+    if (lane < kTile) {
+      if (m > 0.f) atomicMax(&a->max_r_bits, __float_as_uint(m));
+      if (mk) atomicAdd(&a->marked, mk);
+      if (dg) atomicAdd(&a->marked_deg, dg);
+      if (np) atomicAdd(&a->np_flush, np);
+      if (sm != 0.0) atomicAdd(&a->sum_r, sm);
+    }
   }
   __syncthreads();
   p = Partials();
 }
 
-// sum_k coef[k] * max(-x[idx[k]][lane], 0) over [b, e): marked residues.
-__device__ __forceinline__ float dot_pushed(const uint32_t* __restrict__ idx,
-                                            const float* __restrict__ coef, uint32_t b, uint32_t e,
-                                            const float* __restrict__ x, uint32_t lane) {
-  float s = 0.f;
-  for (uint32_t k0 = b; k0 < e; k0 += 32) {
-    const uint32_t n = min(32u, e - k0);
-    uint32_t mi = 0;
-    float mc = 0.f;
-    if (lane < n) { mi = idx[k0 + lane]; mc = coef[k0 + lane]; }
-#pragma unroll 8
-    for (uint32_t j = 0; j < n; ++j) {
-      const uint32_t u = __shfl_sync(kFull, mi, j);
-      const float cc = __shfl_sync(kFull, mc, j);
-      s = fmaf(cc, fmaxf(-x[(size_t)u * kTile + lane], 0.f), s);
-    }
-  }
-  return s;
-}
-
-// Same for attribute rows: coefficient w(u,a) * rnorm_u[u].
-template <typename WA>
-__device__ __forceinline__ float dot_pushed_attr(const DevGraph& g, uint32_t b, uint32_t e,
-                                                 const float* __restrict__ x, uint32_t lane) {
-  float s = 0.f;
-  for (uint32_t k0 = b; k0 < e; k0 += 32) {
-    const uint32_t n = min(32u, e - k0);
-    uint32_t mi = 0;
-    float mc = 0.f;
-    if (lane < n) {
-      mi = g.au_idx[k0 + lane];
-      mc = wload<WA>(g.au_w, k0 + lane) * g.rnorm_u[mi];
-    }
-#pragma unroll 8
-    for (uint32_t j = 0; j < n; ++j) {
-      const uint32_t u = __shfl_sync(kFull, mi, j);
-      const float cc = __shfl_sync(kFull, mc, j);
-      s = fmaf(cc, fmaxf(-x[(size_t)u * kTile + lane], 0.f), s);
-    }
-  }
-  return s;
-}
-
-// sum_k w[k] * x[idx[k]][lane] over [b, e).
-template <typename W>
-__device__ __forceinline__ float dot_plain(const uint32_t* __restrict__ idx, const void* w,
-                                           uint32_t b, uint32_t e, const float* __restrict__ x,
-                                           uint32_t lane) {
-  float s = 0.f;
-  for (uint32_t k0 = b; k0 < e; k0 += 32) {
-    const uint32_t n = min(32u, e - k0);
-    uint32_t mi = 0;
-    float mc = 0.f;
-    if (lane < n) { mi = idx[k0 + lane]; mc = wload<W>(w, k0 + lane); }
-#pragma unroll 8
-    for (uint32_t j = 0; j < n; ++j) {
-      const uint32_t v = __shfl_sync(kFull, mi, j);
-      const float cc = __shfl_sync(kFull, mc, j);
-      s = fmaf(cc, x[(size_t)v * kTile + lane], s);
-    }
-  }
-  return s;
-}
-
-// Split-row combine: returns true (warp-uniform) for the chunk that finishes
-// the row, with the row total in *tot.
-__device__ __forceinline__ bool split_combine(const TileBuf& t, uint32_t slot, uint32_t nch,
-                                              float s, uint32_t lane, float* tot) {
-  atomicAdd(&t.split_acc[(size_t)slot * kTile + lane], s);
-  __threadfence();
-  __syncwarp();
-  uint32_t last = 0;
-  if (lane == 0) last = atomicAdd(&t.split_cnt[slot], 1u) == nch - 1;
-  last = __shfl_sync(kFull, last, 0);
-  if (last) {
-    __threadfence();
-    *tot = atomicExch(&t.split_acc[(size_t)slot * kTile + lane], 0.f);
-    if (lane == 0) t.split_cnt[slot] = 0;
-  }
-  return last != 0;
-}
-
-// Phase 1: t_V and t_A for the 32 queries of the tile.
-template <typename WA>
-__device__ __forceinline__ void bphase1(const BCtx& c, Partials& part) {
-  const DevGraph& g = c.g;
-  const uint32_t lane = c.lane;
-  const uint32_t nv = g.b_v.n_items, total = nv + g.b_a.n_items;
-  for (uint32_t it = c.gw; it < total; it += c.nw) {
-    const bool is_a = it >= nv;
-    const uint4 item = is_a ? g.b_a.items[it - nv] : g.b_v.items[it];
-    const uint32_t* off = is_a ? g.au_off : g.vu_off;
-    uint32_t r0, r1;
-    if (item.y & (kItemLong | kItemSplit)) { r0 = item.x; r1 = item.x + 1; }
-    else { r0 = item.x; r1 = item.x + item.y; }
-    for (uint32_t row = r0; row < r1; ++row) {
-      uint32_t b = off[row], e = off[row + 1];
-      if (item.y & (kItemLong | kItemSplit)) { e = b + item.w; b = b + item.z; }
-      float s = is_a ? dot_pushed_attr<WA>(g, b, e, c.t.r_u, lane)
-                     : dot_pushed(g.vu_idx, g.vu_c, b, e, c.t.r_u, lane);
-      if (item.y & kItemSplit) {
-        const uint32_t sl = item.y & kItemMask;
-        const uint32_t slot = sl + (is_a ? g.b_v.n_split : 0);
-        const uint32_t nch = is_a ? g.b_a.split_nchunks[sl] : g.b_v.split_nchunks[sl];
-        float tot;
-        if (!split_combine(c.t, slot, nch, s, lane, &tot)) continue;
-        s = tot;
-      }
-      if (!is_a) {
-        c.t.t_v[(size_t)row * kTile + lane] = s;
-        if (s > 0.f) part.np_flush += g.vu_off[row + 1] - g.vu_off[row];
-      } else {
-        const float tv = g.k_attr * g.cnorm_a[row] * s;
-        c.t.t_a[(size_t)row * kTile + lane] = tv;
-        if (tv > 0.f) part.np_flush += g.au_off[row + 1] - g.au_off[row];
-      }
-    }
-  }
-}
+// ------------------------------------------------------------------------
+// Pull phases with row groups: a warp is 4 groups of 8 lanes; a group owns
+// one row (or one chunk of a long row) and each of its lanes owns 4 of the
+// tile's 32 queries (lane l of the group: queries 4l .. 4l+3).  One gather
+// is a float4 load per lane, so the group reads the 32 queries' values of a
+// neighbour as one 128-byte line and one warp instruction moves 4 lines.
+// Entries are staged 32 at a time (4 per lane, coalesced), then gathered 8
+// at a time with all 8 loads in flight before they are consumed.
+constexpr int kQL = 4;                 // queries per lane
+constexpr int kGL = kTile / kQL;       // lanes per row group (one 128- or 64-byte line)
+constexpr int kGPW = 32 / kGL;         // row groups per warp
+constexpr int kSlots = 32 / kGL;       // staged entries per lane per 32-entry stage
+static_assert(kTile == 16 || kTile == 32, "tile of 16 or 32 queries");
+#ifndef AHPP_BATCH_WAVES
+#define AHPP_BATCH_WAVES 1        // 8-entry gather waves issued together (1 or 2)
+#endif
+#ifndef AHPP_BATCH_MINB
+#define AHPP_BATCH_MINB 3         // resident blocks per SM the register budget targets
+#endif
 
 struct LaneCtl {
   double eps_f;
   unsigned long long n_p, pushes;
   uint32_t rounds, switch_round;
-  int phase, status, active;
+  int phase, status, active, valid;
 };
 
-__device__ __forceinline__ void bepilogue2(const BCtx& c, const LaneCtl& L, uint32_t u, float s,
-                                           uint32_t cnt, Partials& part) {
-  if (!L.active) return;
-  const size_t i = (size_t)u * kTile + c.lane;
-  const float r_old = c.t.r_u[i];
-  float kept = r_old;
-  if (r_old < 0.f) {
-    const float add = c.g.alpha * (-r_old);
-    if (c.p.kahan) {
-      float pv = c.t.pi[i], pc = c.t.pic[i];
-      kahan_add(pv, pc, add);
-      c.t.pi[i] = pv; c.t.pic[i] = pc;
-    } else {
-      c.t.pi[i] += add;
-    }
-    kept = 0.f;
-  }
-  const float r_new = kept + s;
-  part.max_r = fmaxf(part.max_r, r_new);
-  part.sum_r += (double)r_new;
-  double th;
-  if (c.p.algo == kAlgoAPP) th = L.eps_f * (double)cnt;
-  else th = (L.phase == kPhaseSync) ? 0.0 : L.eps_f;
-  if ((double)r_new > th) {
-    c.t.r_u[i] = -r_new;
-    part.marked += 1;
-    part.marked_deg += cnt;
-  } else {
-    c.t.r_u[i] = r_new;
-  }
+// Smallest float f with (r > th) <=> (r >= f) for every float r: the mark
+// test r > th of Algorithm 4 taken exactly against the FP64 threshold.
+__device__ __forceinline__ float threshold_up(double th) {
+  float f = (float)th;
+  if ((double)f <= th) f = nextafterf(f, INFINITY);
+  return f;
 }
 
-// Phase 2: new residues of every U node for the 32 queries.
-template <typename WA>
-__device__ __forceinline__ void bphase2(const BCtx& c, const LaneCtl& L, Partials& part) {
-  const DevGraph& g = c.g;
-  const uint32_t lane = c.lane;
-  for (uint32_t it = c.gw; it < g.b_u.n_items; it += c.nw) {
-    const uint4 item = g.b_u.items[it];
-    if (item.y & (kItemLong | kItemSplit)) {
-      const uint32_t u = item.x;
-      const uint32_t b1 = g.uv_off[u], dv = g.uv_off[u + 1] - b1;
-      const uint32_t b2 = g.ua_off[u], da = g.ua_off[u + 1] - b2;
-      // chunk [z, w) of the combined list (V neighbours, then attributes)
-      float s = 0.f;
-      const uint32_t z = item.z, w = item.w;
-      if (z < dv) s += dot_plain<float>(g.uv_idx, g.uv_w, b1 + z, b1 + min(w, dv), c.t.t_v, lane);
-      if (w > dv)
-        s += dot_plain<WA>(g.ua_idx, g.ua_w, b2 + (z > dv ? z - dv : 0), b2 + (w - dv), c.t.t_a, lane);
-      if (item.y & kItemSplit) {
-        const uint32_t sl = item.y & kItemMask;
-        const uint32_t slot = sl + g.b_v.n_split + g.b_a.n_split;
-        float tot;
-        if (!split_combine(c.t, slot, g.b_u.split_nchunks[sl], s, lane, &tot)) continue;
-        s = tot;
-      }
-      bepilogue2(c, L, u, s, dv + da, part);
-    } else {
-      for (uint32_t u = item.x; u < item.x + item.y; ++u) {
-        const uint32_t b1 = g.uv_off[u], e1 = g.uv_off[u + 1];
-        const uint32_t b2 = g.ua_off[u], e2 = g.ua_off[u + 1];
-        float s = dot_plain<float>(g.uv_idx, g.uv_w, b1, e1, c.t.t_v, lane);
-        s += dot_plain<WA>(g.ua_idx, g.ua_w, b2, e2, c.t.t_a, lane);
-        bepilogue2(c, L, u, s, (e1 - b1) + (e2 - b2), part);
-      }
+// Gathered state (r_U rows in phase 1, t_V / t_A rows in phase 2) is loaded
+// with the L2 evict-last policy so that the streamed graph arrays (loaded
+// evict-first) do not push it out of L2 during a phase.
+__device__ __forceinline__ uint64_t policy_keep() {
+  uint64_t pol;
+  asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(pol));
+  return pol;
+}
+__device__ __forceinline__ float4 ld_keep4(const float* p, uint64_t pol) {
+  float4 v;
+  asm volatile("ld.global.L2::cache_hint.v4.f32 {%0, %1, %2, %3}, [%4], %5;"
+               : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w) : "l"(p), "l"(pol));
+  return v;
+}
+
+__device__ __forceinline__ float4 f4_fma(float c, float4 x, float4 a) {
+  return make_float4(fmaf(c, x.x, a.x), fmaf(c, x.y, a.y), fmaf(c, x.z, a.z), fmaf(c, x.w, a.w));
+}
+
+// Sum over the entries [b, e) of this group's row of coef(k) * gather(idx(k)).
+// Called by the whole warp (control is warp-uniform; rounds = the warp's
+// maximum number of 32-entry stages); a group with b == e adds nothing.
+template <typename LoadF, typename GatherF>
+__device__ __forceinline__ float4 group_accum(uint32_t b, uint32_t e, uint32_t stages, uint32_t gl,
+                                              LoadF load, GatherF gather) {
+  float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
+  for (uint32_t st = 0; st < stages; ++st) {
+    const uint32_t k0 = b + st * 32;
+    const uint32_t n = k0 < e ? min(32u, e - k0) : 0u;
+    uint32_t mi[kSlots];
+    float mc[kSlots];
+#pragma unroll
+    for (int s = 0; s < kSlots; ++s) {
+      const uint32_t j = gl + kGL * s;
+      mi[s] = 0; mc[s] = 0.f;
+      if (j < n) load(k0 + j, mi[s], mc[s]);
+    }
+    constexpr int W = AHPP_BATCH_WAVES;
+#pragma unroll
+    for (int s = 0; s < kSlots; s += W) {
+      float4 x[W * kGL];
+#pragma unroll
+      for (int h = 0; h < W; ++h)
+#pragma unroll
+        for (int t = 0; t < kGL; ++t) {
+          const uint32_t id = __shfl_sync(kFull, mi[s + h], t, kGL);
+          x[h * kGL + t] = (uint32_t)(kGL * (s + h) + t) < n ? gather(id) : make_float4(0.f, 0.f, 0.f, 0.f);
+        }
+#pragma unroll
+      for (int h = 0; h < W; ++h)
+#pragma unroll
+        for (int t = 0; t < kGL; ++t)
+          acc = f4_fma(__shfl_sync(kFull, mc[s + h], t, kGL), x[h * kGL + t], acc);
     }
   }
+  return acc;
+}
+
+__device__ __forceinline__ uint32_t warp_max_u32(uint32_t v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = max(v, __shfl_xor_sync(kFull, v, o));
+  return v;
+}
+
+// Per-query partials of one thread (its 4 queries) summed over the warp's 4
+// groups and the block's warps, then added to acc[q] (one atomic per query
+// and field per block).
+struct Q4Partials {
+  float max_r[kQL] = {0.f, 0.f, 0.f, 0.f};
+  uint32_t marked[kQL] = {0, 0, 0, 0};
+  uint32_t mdeg[kQL] = {0, 0, 0, 0};
+  uint32_t np[kQL] = {0, 0, 0, 0};
+};
+
+__device__ __forceinline__ void flush_q4(Q4Partials& p, RAcc* acc) {
+  __shared__ float s_max[kWarps][32];
+  __shared__ uint32_t s_mk[kWarps][32], s_dg[kWarps][32], s_np[kWarps][32];
+  const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int j = 0; j < kQL; ++j) {
+#pragma unroll
+    for (int o = kGL; o < 32; o <<= 1) {
+      p.max_r[j] = fmaxf(p.max_r[j], __shfl_xor_sync(kFull, p.max_r[j], o));
+      p.marked[j] += __shfl_xor_sync(kFull, p.marked[j], o);
+      p.mdeg[j] += __shfl_xor_sync(kFull, p.mdeg[j], o);
+      p.np[j] += __shfl_xor_sync(kFull, p.np[j], o);
+    }
+  }
+  if (lane < kGL) {
+#pragma unroll
+    for (int j = 0; j < kQL; ++j) {
+      const uint32_t q = lane * kQL + j;
+      s_max[warp][q] = p.max_r[j]; s_mk[warp][q] = p.marked[j];
+      s_dg[warp][q] = p.mdeg[j]; s_np[warp][q] = p.np[j];
+    }
+  }
+  __syncthreads();
+  if (warp == 0 && lane < kTile) {
+    float m = 0.f;
+    uint32_t mk = 0;
+    unsigned long long dg = 0, np = 0;
+    for (int w = 0; w < kWarps; ++w) {
+      m = fmaxf(m, s_max[w][lane]); mk += s_mk[w][lane];
+      dg += s_dg[w][lane]; np += s_np[w][lane];
+    }
+    RAcc* a = &acc[lane];
+    if (m > 0.f) atomicMax(&a->max_r_bits, __float_as_uint(m));
+    if (mk) atomicAdd(&a->marked, mk);
+    if (dg) atomicAdd(&a->marked_deg, dg);
+    if (np) atomicAdd(&a->np_flush, np);
+  }
+  __syncthreads();
+  p = Q4Partials();
+}
+
+// Combine a chunk of a split row (group-collective): returns true in every
+// lane of the group whose chunk finishes the row, with the row total.
+__device__ __forceinline__ bool split_combine4(const TileBuf& t, uint32_t slot, uint32_t nch,
+                                               float4 s, uint32_t gl, unsigned gmask, float4* tot) {
+  float* a = &t.split_acc[(size_t)slot * kTile + kQL * gl];
+  atomicAdd(reinterpret_cast<float4*>(a), s);
+  __threadfence();
+  __syncwarp(gmask);
+  uint32_t last = 0;
+  if (gl == 0) last = atomicAdd(&t.split_cnt[slot], 1u) == nch - 1;
+  last = __shfl_sync(gmask, last, 0, kGL);
+  if (last) {
+    __threadfence();
+    *tot = __ldcg(reinterpret_cast<const float4*>(a));
+    __stcg(reinterpret_cast<float4*>(a), make_float4(0.f, 0.f, 0.f, 0.f));
+    __syncwarp(gmask);
+    if (gl == 0) t.split_cnt[slot] = 0;
+  }
+  return last != 0;
+}
+
+// Unit u of a row space: units [0, n_items) are chunks of the long rows
+// (items[u] = {row, kItemSplit | slot, z, w}); units n_items.. are the short
+// rows n_long.. one each.
+struct Unit {
+  uint32_t row, b, e;     // row and local entry range
+  uint32_t slot;          // split slot or ~0
+};
+
+__device__ __forceinline__ Unit unit_of(const ItemList& L, uint32_t u, const uint32_t* off) {
+  Unit x;
+  if (u < L.n_items) {
+    const uint4 it = L.items[u];
+    x.row = it.x; x.b = it.z; x.e = it.w; x.slot = it.y & kItemMask;
+  } else {
+    x.row = L.n_long + (u - L.n_items);
+    x.b = 0; x.e = off[x.row + 1] - off[x.row]; x.slot = 0xffffffffu;
+  }
+  return x;
+}
+
+// Phase 1: t_V and t_A of the tile's 32 queries.
+//   t_V[v] = sum_u c_uv(u,v) p_u;   t_A[a] = k_attr cnorm_a[a] sum_u w(u,a) rnorm_u[u] p_u
+template <typename WA>
+__device__ __forceinline__ void gphase1(const BCtx& c, RAcc* A) {
+  const DevGraph& g = c.g;
+  const uint32_t lane = c.lane, gl = lane & (kGL - 1), gi = lane / kGL;
+  const unsigned gmask = ((1u << kGL) - 1u) << (gi * kGL);
+  const float* __restrict__ r_u = c.t.r_u;
+  const uint64_t pol = policy_keep();
+  auto gp = [&](uint32_t u) {
+    const float4 x = ld_keep4(r_u + (size_t)u * kTile + kQL * gl, pol);
+    return make_float4(fmaxf(-x.x, 0.f), fmaxf(-x.y, 0.f), fmaxf(-x.z, 0.f), fmaxf(-x.w, 0.f));
+  };
+  Q4Partials part;
+  const uint32_t nuv = g.b_v.n_items + (g.n_v - g.b_v.n_long);
+  const uint32_t nua = g.b_a.n_items + (g.n_a - g.b_a.n_long);
+  const uint32_t total = nuv + nua;
+  for (uint32_t base = c.gw * kGPW; base < total; base += c.nw * kGPW) {
+    const uint32_t uix = base + gi;
+    const bool ok = uix < total;
+    const bool is_a = ok && uix >= nuv;
+    Unit un{0, 0, 0, 0xffffffffu};
+    const uint32_t* off = is_a ? g.au_off : g.vu_off;
+    if (ok) un = is_a ? unit_of(g.b_a, uix - nuv, g.au_off) : unit_of(g.b_v, uix, g.vu_off);
+    const uint32_t b = ok ? off[un.row] + un.b : 0, e = ok ? off[un.row] + un.e : 0;
+    const uint32_t stages = warp_max_u32(is_a ? 0u : (e - b + 31) / 32);
+    // V rows and attribute rows in one warp: both gathers run, each group
+    // keeps the one of its own kind (ranges are empty for the other)
+    const float4 sv = group_accum(is_a ? 0u : b, is_a ? 0u : e, stages, gl,
+        [&](uint32_t k, uint32_t& i, float& w) { i = __ldcs(g.vu_idx + k); w = __ldcs(g.vu_c + k); }, gp);
+    const uint32_t stages_a = warp_max_u32(is_a ? (e - b + 31) / 32 : 0u);
+    const float4 sa = group_accum(is_a ? b : 0u, is_a ? e : 0u, stages_a, gl,
+        [&](uint32_t k, uint32_t& i, float& w) {
+          i = __ldcs(g.au_idx + k);
+          w = wload<WA>(g.au_w, k) * g.rnorm_u[i];
+        }, gp);
+    if (!ok) continue;
+    float4 s = is_a ? sa : sv;
+    if (un.slot != 0xffffffffu) {
+      const uint32_t slot = un.slot + (is_a ? g.b_v.n_split : 0);
+      const uint32_t nch = is_a ? g.b_a.split_nchunks[un.slot] : g.b_v.split_nchunks[un.slot];
+      float4 tot;
+      if (!split_combine4(c.t, slot, nch, s, gl, gmask, &tot)) continue;
+      s = tot;
+    }
+    const uint32_t R = un.row;
+    if (!is_a) {
+      *reinterpret_cast<float4*>(c.t.t_v + (size_t)R * kTile + kQL * gl) = s;
+      const uint32_t d = g.vu_off[R + 1] - g.vu_off[R];
+      part.np[0] += s.x > 0.f ? d : 0; part.np[1] += s.y > 0.f ? d : 0;
+      part.np[2] += s.z > 0.f ? d : 0; part.np[3] += s.w > 0.f ? d : 0;
+    } else {
+      const float f = g.k_attr * g.cnorm_a[R];
+      const float4 tv = make_float4(f * s.x, f * s.y, f * s.z, f * s.w);
+      *reinterpret_cast<float4*>(c.t.t_a + (size_t)R * kTile + kQL * gl) = tv;
+      const uint32_t d = g.au_off[R + 1] - g.au_off[R];
+      part.np[0] += tv.x > 0.f ? d : 0; part.np[1] += tv.y > 0.f ? d : 0;
+      part.np[2] += tv.z > 0.f ? d : 0; part.np[3] += tv.w > 0.f ? d : 0;
+    }
+  }
+  flush_q4(part, A);
+}
+
+// Residue update of row u for this lane's 4 queries: reserve update of the
+// queries that pushed u this round, then the mark for the next round.
+__device__ __forceinline__ void gepilogue2(const BCtx& c, uint32_t u, float4 s, uint32_t cnt,
+                                           const float* th, const int* act, const LaneCtl* app_ctl,
+                                           Q4Partials& part) {
+  if (!(act[0] | act[1] | act[2] | act[3])) return;
+  const uint32_t gl = c.lane & (kGL - 1);
+  const size_t i = (size_t)u * kTile + kQL * gl;
+  float4* rp = reinterpret_cast<float4*>(c.t.r_u + i);
+  float4* pp = reinterpret_cast<float4*>(c.t.pi + i);
+  float4* cp = reinterpret_cast<float4*>(c.t.pic + i);
+  float4 r = *rp;
+  float4 pv = __ldcs(pp), pc = __ldcs(cp);
+  float* rr = &r.x;
+  float* pvv = &pv.x;
+  float* pcc = &pc.x;
+  const float* ss = &s.x;
+  bool pushed_any = false;
+#pragma unroll
+  for (int j = 0; j < kQL; ++j) {
+    if (!act[j]) continue;
+    float kept = rr[j];
+    if (kept < 0.f) {
+      const float add = c.g.alpha * (-kept);
+      if (c.p.kahan) kahan_add(pvv[j], pcc[j], add);
+      else pvv[j] += add;
+      kept = 0.f;
+      pushed_any = true;
+    }
+    const float r_new = kept + ss[j];
+    part.max_r[j] = fmaxf(part.max_r[j], r_new);
+    const bool mark = app_ctl ? (double)r_new > app_ctl[kQL * gl + j].eps_f * (double)cnt
+                              : r_new >= th[j];
+    if (mark) {
+      rr[j] = -r_new;
+      part.marked[j] += 1;
+      part.mdeg[j] += cnt;
+    } else {
+      rr[j] = r_new;
+    }
+  }
+  *rp = r;
+  if (pushed_any) { __stcs(pp, pv); __stcs(cp, pc); }
+}
+
+// Phase 2: new residues of every U node for the tile's 32 queries.
+template <typename WA>
+__device__ __forceinline__ void gphase2(const BCtx& c, const LaneCtl* ctl, RAcc* A) {
+  const DevGraph& g = c.g;
+  const uint32_t lane = c.lane, gl = lane & (kGL - 1), gi = lane / kGL;
+  const unsigned gmask = ((1u << kGL) - 1u) << (gi * kGL);
+  const bool app = c.p.algo == kAlgoAPP;
+  // mark thresholds and activity of this lane's 4 queries
+  float th[kQL];
+  int act[kQL];
+#pragma unroll
+  for (int j = 0; j < kQL; ++j) {
+    const LaneCtl& q = ctl[kQL * gl + j];
+    act[j] = q.active;
+    th[j] = app ? 0.f : threshold_up(q.phase == kPhaseSync ? 0.0 : q.eps_f);
+  }
+  const float* __restrict__ t_v = c.t.t_v;
+  const float* __restrict__ t_a = c.t.t_a;
+  const uint64_t pol = policy_keep();
+  auto gv = [&](uint32_t v) { return ld_keep4(t_v + (size_t)v * kTile + kQL * gl, pol); };
+  auto ga = [&](uint32_t a) { return ld_keep4(t_a + (size_t)a * kTile + kQL * gl, pol); };
+  Q4Partials part;
+  const uint32_t total = g.b_u.n_items + (g.n_u - g.b_u.n_long);
+  for (uint32_t base = c.gw * kGPW; base < total; base += c.nw * kGPW) {
+    const uint32_t uix = base + gi;
+    const bool ok = uix < total;
+    uint32_t u = 0, z = 0, w = 0, slot = 0xffffffffu, b1 = 0, dv = 0, b2 = 0, da = 0;
+    if (ok) {
+      if (uix < g.b_u.n_items) {
+        const uint4 it = g.b_u.items[uix];
+        u = it.x; z = it.z; w = it.w; slot = it.y & kItemMask;
+      } else {
+        u = g.b_u.n_long + (uix - g.b_u.n_items);
+      }
+      b1 = g.uv_off[u]; dv = g.uv_off[u + 1] - b1;
+      b2 = g.ua_off[u]; da = g.ua_off[u + 1] - b2;
+      if (slot == 0xffffffffu) { z = 0; w = dv + da; }
+    }
+    // chunk [z, w) of the combined list: V neighbours first, then attributes
+    const uint32_t vb = b1 + min(z, dv), ve = b1 + min(w, dv);
+    const uint32_t ab = b2 + (z > dv ? z - dv : 0), ae = b2 + (w > dv ? w - dv : 0);
+    const uint32_t sv = warp_max_u32((ve - vb + 31) / 32), sa = warp_max_u32((ae - ab + 31) / 32);
+    float4 s = group_accum(vb, ve, sv, gl,
+        [&](uint32_t k, uint32_t& i, float& wt) { i = __ldcs(g.uv_idx + k); wt = __ldcs(g.uv_w + k); }, gv);
+    const float4 s2 = group_accum(ab, ae, sa, gl,
+        [&](uint32_t k, uint32_t& i, float& wt) { i = __ldcs(g.ua_idx + k); wt = wload<WA>(g.ua_w, k); }, ga);
+    if (!ok) continue;
+    s = make_float4(s.x + s2.x, s.y + s2.y, s.z + s2.z, s.w + s2.w);
+    if (slot != 0xffffffffu) {
+      const uint32_t sl = slot + g.b_v.n_split + g.b_a.n_split;
+      float4 tot;
+      if (!split_combine4(c.t, sl, g.b_u.split_nchunks[slot], s, gl, gmask, &tot)) continue;
+      s = tot;
+    }
+    gepilogue2(c, u, s, dv + da, th, act, app ? ctl : nullptr, part);
+  }
+  flush_q4(part, A);
 }
 
 __device__ __forceinline__ double bbudget(const BatchParams& p, double eps_f, double M) {
@@ -267,10 +431,17 @@ __device__ __forceinline__ unsigned long long score_key(float score, uint32_t ca
 }  // namespace
 
 template <typename WA>
-__global__ void __launch_bounds__(kThreads, 3)
+__global__ void __launch_bounds__(kThreads, AHPP_BATCH_MINB)
 k_batch(const __grid_constant__ DevGraph g, const __grid_constant__ BatchState st,
         const __grid_constant__ BatchParams p) {
   extern __shared__ unsigned char smem[];
+  // Per-query control of the current tile, one entry per lane / query.  Warp 0
+  // of every block makes the decisions (all blocks read the same round
+  // accumulators after a barrier, so they agree); the phases read it here.
+  __shared__ LaneCtl s_ctl[kTile];
+  __shared__ unsigned long long s_mdeg[kTile];
+  __shared__ int s_switch[kTile];
+  __shared__ int s_flag;
   const uint32_t groups = p.groups;
   const uint32_t nbg = gridDim.x / groups;              // blocks per group
   const uint32_t grp = blockIdx.x / nbg;
@@ -280,6 +451,8 @@ k_batch(const __grid_constant__ DevGraph g, const __grid_constant__ BatchState s
   BCtx c{g, tb, p, (bid * kThreads + threadIdx.x) >> 5, (nbg * kThreads) >> 5,
          bid * kThreads + threadIdx.x, nbg * kThreads, threadIdx.x & 31u};
   const uint32_t lane = c.lane;
+  const bool lq = lane < (uint32_t)kTile;               // this lane stands for a query
+  const bool warp0 = threadIdx.x < 32;
   const bool app = p.algo == kAlgoAPP;
   const uint32_t n_tiles = (p.n + kTile - 1) / kTile;
   const uint32_t n_split = g.b_v.n_split + g.b_a.n_split + g.b_u.n_split;
@@ -298,29 +471,31 @@ k_batch(const __grid_constant__ DevGraph g, const __grid_constant__ BatchState s
     if (!grid_sync(tb.bar, nbg)) return;
 
     const uint32_t qi = tile * kTile + lane;
-    const bool in_range = qi < p.n;
-    // ids and eps come from device memory: an invalid one disables its lane
-    const bool bad = in_range && (p.q[qi] >= g.n_u || !(p.eps[qi] > 0.0));
-    const bool valid = in_range && !bad;
-    uint32_t q_new = 0;
-    LaneCtl L{0.0, 0, 0, 0, 0, kPhaseAsync, bad ? kStatusBadArg : kStatusOk, 0};
-    if (valid) {
-      q_new = p.u_old2new[p.q[qi]];
-      const double eps = p.eps[qi];
-      L.eps_f = app ? eps / (double)p.e_tot : eps / p.lambda;
-      L.active = 1;
-    }
-    if (bid == 0 && threadIdx.x < 32 && valid) {
-      const uint32_t cnt = (g.uv_off[q_new + 1] - g.uv_off[q_new]) + (g.ua_off[q_new + 1] - g.ua_off[q_new]);
-      const double th = app ? L.eps_f * (double)cnt : L.eps_f;
-      RAcc* a0 = &tb.racc[2 * kTile + lane];
-      if (1.0 > th) {
-        tb.r_u[(size_t)q_new * kTile + lane] = -1.f;
-        a0->marked = 1;
-        a0->marked_deg = cnt;
-      } else {
-        tb.r_u[(size_t)q_new * kTile + lane] = 1.f;
+    const bool in_range = lq && qi < p.n;
+    if (warp0) {
+      // ids and eps come from device memory: an invalid one disables its lane
+      const bool bad = in_range && (p.q[qi] >= g.n_u || !(p.eps[qi] > 0.0));
+      LaneCtl L{0.0, 0, 0, 0, 0, kPhaseAsync, bad ? kStatusBadArg : kStatusOk, 0, 0};
+      if (in_range && !bad) {
+        const uint32_t q_new = p.u_old2new[p.q[qi]];
+        const double eps = p.eps[qi];
+        L.eps_f = app ? eps / (double)p.e_tot : eps / p.lambda;
+        L.active = 1;
+        L.valid = 1;
+        if (bid == 0) {
+          const uint32_t cnt = (g.uv_off[q_new + 1] - g.uv_off[q_new]) + (g.ua_off[q_new + 1] - g.ua_off[q_new]);
+          const double th = app ? L.eps_f * (double)cnt : L.eps_f;
+          RAcc* a0 = &tb.racc[2 * kTile + lane];
+          if (1.0 > th) {
+            tb.r_u[(size_t)q_new * kTile + lane] = -1.f;
+            a0->marked = 1;
+            a0->marked_deg = cnt;
+          } else {
+            tb.r_u[(size_t)q_new * kTile + lane] = 1.f;
+          }
+        }
       }
+      if (lq) s_ctl[lane] = L;
     }
     if (!grid_sync(tb.bar, nbg)) return;
 
@@ -330,44 +505,64 @@ k_batch(const __grid_constant__ DevGraph g, const __grid_constant__ BatchState s
     for (;;) {
       RAcc* A = &tb.racc[(tround % 3) * kTile];
       const RAcc* P = &tb.racc[((tround + 2) % 3) * kTile];
-      const uint32_t marked = __ldcg(&P[lane].marked);
-      const unsigned long long marked_deg = __ldcg(&P[lane].marked_deg);
-      if (L.active && (L.phase == kPhaseDone || marked == 0)) { L.phase = kPhaseDone; L.active = 0; }
-      if (L.active && L.rounds >= p.max_rounds) { L.status = kStatusCap; L.active = 0; }
-      if (!__any_sync(kFull, L.active)) break;
+      if (warp0) {
+        LaneCtl L{};
+        if (lq) {
+          L = s_ctl[lane];
+          const uint32_t marked = __ldcg(&P[lane].marked);
+          s_mdeg[lane] = __ldcg(&P[lane].marked_deg);
+          if (L.active && (L.phase == kPhaseDone || marked == 0)) { L.phase = kPhaseDone; L.active = 0; }
+          if (L.active && L.rounds >= p.max_rounds) { L.status = kStatusCap; L.active = 0; }
+          if (L.active) L.pushes += marked;
+          s_ctl[lane] = L;
+        }
+        const int any = __any_sync(kFull, L.active);
+        if (lane == 0) s_flag = any;
+      }
+      __syncthreads();
+      if (!s_flag) break;
       if (bid == 0 && threadIdx.x < kTile) tb.racc[((tround + 1) % 3) * kTile + threadIdx.x] = RAcc{};
-      if (L.active) L.pushes += marked;
 
-      bphase1<WA>(c, part);
-      flush_lane_partials(part, A);
+      gphase1<WA>(c, A);
       if (!grid_sync(tb.bar, nbg)) { wait_fail = true; break; }
-      bphase2<WA>(c, L, part);
-      flush_lane_partials(part, A);
+      gphase2<WA>(c, s_ctl, A);
       if (!grid_sync(tb.bar, nbg)) { wait_fail = true; break; }
       ++tround;
 
-      bool switched = false;
-      if (L.active) {
-        ++L.rounds;
-        const float M = __uint_as_float(__ldcg(&A[lane].max_r_bits));
-        L.n_p += marked_deg + __ldcg(&A[lane].np_flush);
-        if (!app) {
-          if ((double)M <= L.eps_f) {
-            L.phase = kPhaseDone;
-            L.active = 0;
-          } else if (L.phase == kPhaseAsync && (double)L.n_p >= bbudget(p, L.eps_f, (double)M)) {
-            L.phase = kPhaseSync;
-            L.switch_round = L.rounds + 1;
-            switched = true;
+      if (warp0) {
+        LaneCtl L{};
+        if (lq) L = s_ctl[lane];
+        int switched = 0;
+        if (L.active) {
+          ++L.rounds;
+          const float M = __uint_as_float(__ldcg(&A[lane].max_r_bits));
+          L.n_p += s_mdeg[lane] + __ldcg(&A[lane].np_flush);
+          if (!app) {
+            if ((double)M <= L.eps_f) {
+              L.phase = kPhaseDone;
+              L.active = 0;
+            } else if (L.phase == kPhaseAsync && (double)L.n_p >= bbudget(p, L.eps_f, (double)M)) {
+              L.phase = kPhaseSync;
+              L.switch_round = L.rounds + 1;
+              switched = 1;
+            }
           }
         }
+        if (lq) {
+          s_ctl[lane] = L;
+          s_switch[lane] = switched;
+        }
+        const int any = __any_sync(kFull, switched);
+        if (lane == 0) s_flag = any;
       }
-      if (__any_sync(kFull, switched)) {
+      __syncthreads();
+      if (s_flag) {
         // first synchronous round pushes every positive residue of that query
+        const bool sw = lq && s_switch[lane] != 0;
         for (size_t u = c.gw; u < g.n_u; u += c.nw) {
-          const size_t i = u * kTile + lane;
-          const float r = tb.r_u[i];
-          if (switched && r > 0.f) {
+          const size_t i = u * kTile + (lq ? lane : 0);
+          const float r = sw ? tb.r_u[i] : 0.f;
+          if (sw && r > 0.f) {
             tb.r_u[i] = -r;
             part.marked += 1;
             part.marked_deg += (g.uv_off[u + 1] - g.uv_off[u]) + (g.ua_off[u + 1] - g.ua_off[u]);
@@ -377,12 +572,14 @@ k_batch(const __grid_constant__ DevGraph g, const __grid_constant__ BatchState s
         if (!grid_sync(tb.bar, nbg)) { wait_fail = true; break; }
       }
     }
-    if (wait_fail) L.status = kStatusWait;
+    if (wait_fail && warp0 && lq) s_ctl[lane].status = kStatusWait;
+    __syncthreads();
+    const bool valid = lq && s_ctl[lane].valid != 0;
 
     // ---- reserves = pi - compensation; per-query sums; dense output
     {
       Partials pr, pp;
-      for (size_t u = c.gw; u < g.n_u; u += c.nw) {
+      for (size_t u = c.gw; lq && u < g.n_u; u += c.nw) {
         const size_t i = u * kTile + lane;
         const float v = fmaxf(tb.pi[i] - tb.pic[i], 0.f);
         tb.pi[i] = v;
@@ -399,12 +596,13 @@ k_batch(const __grid_constant__ DevGraph g, const __grid_constant__ BatchState s
 
     const uint32_t kq = (valid && p.kmax) ? min(min(p.k[qi], p.kmax), g.n_u) : 0u;
     if (bid == 0 && threadIdx.x < kTile && in_range && p.out_stats) {
+      const LaneCtl L = s_ctl[lane];
       ahpp_stats S;
       S.rounds = L.rounds;
       S.switch_round = L.switch_round;
       S.dense_rounds = L.rounds;
-      S.status = (uint32_t)((L.status == kStatusOk && L.phase != kPhaseDone && valid) ? kStatusCap
-                                                                                   : L.status);
+      S.status = (uint32_t)((L.status == kStatusOk && L.phase != kPhaseDone && L.valid) ? kStatusCap
+                                                                                     : L.status);
       S.pushes = L.pushes;
       S.n_p = L.n_p;
       S.reserve_sum = __ldcg(&tb.racc[4 * kTile + lane].sum_r);
@@ -425,7 +623,7 @@ k_batch(const __grid_constant__ DevGraph g, const __grid_constant__ BatchState s
         const int shift = 64 - kRadixBits * (pass + 1);
         for (int i = threadIdx.x; i < kTile * kRadixBins; i += kThreads) sh[i] = 0;
         __syncthreads();
-        if (krem) {
+        if (krem && lq) {
           for (size_t u = c.gw; u < g.n_u; u += c.nw) {
             const unsigned long long key = score_key(tb.pi[u * kTile + lane], p.u_new2old[u]);
             if (pass == 0 || (key >> (shift + kRadixBits)) == prefix)
@@ -437,7 +635,7 @@ k_batch(const __grid_constant__ DevGraph g, const __grid_constant__ BatchState s
         for (int i = threadIdx.x; i < kTile * kRadixBins; i += kThreads)
           if (sh[i]) atomicAdd(&gh[i], sh[i]);
         if (!grid_sync(tb.bar, nbg)) return;
-        if (krem) {
+        if (krem && lq) {
           uint32_t cum = 0;
           int d = kRadixBins - 1;
           for (; d > 0; --d) {
@@ -450,7 +648,7 @@ k_batch(const __grid_constant__ DevGraph g, const __grid_constant__ BatchState s
         }
       }
       // prefix is the exact key of the kq-th largest; keys are distinct
-      if (kq) {
+      if (kq && lq) {
         for (size_t u = c.gw; u < g.n_u; u += c.nw) {
           const unsigned long long key = score_key(tb.pi[u * kTile + lane], p.u_new2old[u]);
           if (key >= prefix) {

@@ -12,7 +12,10 @@
 
 namespace ahpp {
 
-constexpr int kTile = 32;          // queries per tile (one per lane)
+#ifndef AHPP_TILE
+#define AHPP_TILE 32
+#endif
+constexpr int kTile = AHPP_TILE;   // queries per tile (16 or 32; lane q of a warp-per-node loop = query q)
 constexpr int kRadixBits = 8;      // top-k digit width (per-lane histograms of 256 bins)
 constexpr int kRadixBins = 1 << kRadixBits;
 constexpr int kRadixPasses = 64 / kRadixBits;

@@ -181,6 +181,23 @@ HostItems build_items(const std::vector<uint32_t>& deg, const ItemShape& sh) {
   return h;
 }
 
+HostItems build_units(const std::vector<uint32_t>& deg, uint32_t chunk) {
+  HostItems h;
+  const uint32_t n = (uint32_t)deg.size();
+  uint32_t r = 0;
+  while (r < n && deg[r] > chunk) {
+    const uint32_t d = deg[r];
+    const uint32_t nch = (d + chunk - 1) / chunk;
+    const uint32_t slot = (uint32_t)h.split_nchunks.size();
+    h.split_nchunks.push_back(nch);
+    for (uint32_t c = 0; c < nch; ++c)
+      h.items.push_back(make_uint4(r, kItemSplit | slot, c * chunk, std::min(d, (c + 1) * chunk)));
+    ++r;
+  }
+  h.n_long = r;
+  return h;
+}
+
 int build_graph(const ahpp_graph_desc* d, ahpp_graph* g) {
   const ahpp_config& cfg = g->cfg;
   const uint64_t lim = (1ull << 31) - 1;
@@ -286,9 +303,10 @@ int build_graph(const ahpp_graph_desc* d, ahpp_graph* g) {
   for (uint32_t v = 0; v < nV; ++v) dg_v[v] = vu_off[v + 1] - vu_off[v];
   for (uint32_t a = 0; a < nA; ++a) dg_a[a] = au_off[a + 1] - au_off[a];
   const ItemShape s1{64, 32, 0xffffffffu, 2048};
-  const ItemShape sb{256, 0x3fffffffu, 64, 512};
+  const uint32_t kUnitChunk = 256;
   HostItems i1v = build_items(dg_v, s1), i1a = build_items(dg_a, s1), i1u = build_items(dg_u, s1);
-  HostItems ibv = build_items(dg_v, sb), iba = build_items(dg_a, sb), ibu = build_items(dg_u, sb);
+  HostItems ibv = build_units(dg_v, kUnitChunk), iba = build_units(dg_a, kUnitChunk),
+            ibu = build_units(dg_u, kUnitChunk);
 
   // 6. upload
   auto up = [&](const void* src, size_t bytes) -> void* {
@@ -331,6 +349,7 @@ int build_graph(const ahpp_graph_desc* d, ahpp_graph* g) {
     L.n_items = (uint32_t)h.items.size();
     L.n_split = (uint32_t)h.split_nchunks.size();
     L.split_nchunks = (const uint32_t*)up(h.split_nchunks.data(), h.split_nchunks.size() * 4);
+    L.n_long = h.n_long;
   };
   up_items(i1v, G.s1_v); up_items(i1a, G.s1_a); up_items(i1u, G.s1_u);
   up_items(ibv, G.b_v); up_items(iba, G.b_a); up_items(ibu, G.b_u);

@@ -34,6 +34,7 @@ struct HostAdj {
 struct HostItems {
   std::vector<uint4> items;
   std::vector<uint32_t> split_nchunks;
+  uint32_t n_long = 0;
 };
 
 // Work-item shapes.
@@ -45,6 +46,9 @@ struct ItemShape {
 };
 
 HostItems build_items(const std::vector<uint32_t>& deg, const ItemShape& shape);
+// Batched row units: rows longer than `chunk` (a prefix, rows being sorted by
+// degree) become split chunks; every other row is one unit.
+HostItems build_units(const std::vector<uint32_t>& deg, uint32_t chunk);
 
 // Device allocation tracked by the graph.
 struct DevBuf {

@@ -41,6 +41,7 @@ struct ItemList {
   uint32_t n_items = 0;
   uint32_t n_split = 0;                 // split rows
   const uint32_t* split_nchunks = nullptr;
+  uint32_t n_long = 0;                  // batched lists: rows [0, n_long) are chunked
 };
 
 struct DevGraph {
