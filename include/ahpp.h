@@ -182,6 +182,21 @@ int ahpp_query_batch_device(ahpp_graph *g, uint32_t n, const uint32_t *d_q, cons
                             float *d_out_scores, uint32_t *d_out_n, ahpp_stats *d_stats,
                             void *stream);
 
+/* ahpp_query_dense without any device allocation, for callers that cannot
+ * allocate at query time (a framework that owns the whole device memory pool,
+ * or a thread that must not take the device synchronisation cudaMalloc /
+ * cudaFree may cause).  The paper has no counterpart: this is a deployment
+ * variant of the single-query push.  The query's working state lives in one
+ * static device array of 32 MiB per device, held until the process exits;
+ * graphs whose single-query state exceeds it are rejected with AHPP_EINVAL.
+ * Outputs: d_out_pi[n_u] (device, caller ids).  stream: cudaStream_t (NULL =
+ * the graph's).  The call waits for its stream before returning; calls are
+ * serialised because they share the array (overlapping use would race).  The
+ * first call on a device resolves the array's address with that device
+ * current: make it before any stream capture.  Returns AHPP_OK,
+ * AHPP_ENOTCONVERGED, AHPP_EINVAL or AHPP_ECUDA. */
+int ahpp_query_dense_noalloc(ahpp_graph *g, uint32_t q, double eps, float *d_out_pi, void *stream);
+
 /* Device-resident single query (the plain path) on stream (NULL = graph's):
  * d_out_nodes[k], d_out_scores[k], d_out_n[1], d_stats (nullable). */
 int ahpp_query_device(ahpp_graph *g, uint32_t q, double eps, uint32_t k,

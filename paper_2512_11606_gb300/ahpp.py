@@ -99,6 +99,7 @@ SIGNATURES = {
                                                ctypes.c_uint32, _vp, _vp, _vp, _vp, _vp]),
     "ahpp_query_device": (ctypes.c_int, [_vp, ctypes.c_uint32, ctypes.c_double, ctypes.c_uint32,
                                          _vp, _vp, _vp, _vp, _vp]),
+    "ahpp_query_dense_noalloc": (ctypes.c_int, [_vp, ctypes.c_uint32, ctypes.c_double, _vp, _vp]),
     "ahpp_autotune": (ctypes.c_int, [_vp, ctypes.c_uint32, _u32p, ctypes.c_double]),
     "ahpp_server_start": (ctypes.c_int, [_vp, ctypes.POINTER(ServerOpts), ctypes.POINTER(_vp)]),
     "ahpp_submit": (ctypes.c_int, [_vp, ctypes.c_uint32, ctypes.c_double, ctypes.c_uint32,
@@ -277,6 +278,14 @@ class Graph:
             self._h, q, eps, k, nodes_t.data_ptr(), scores_t.data_ptr(), n_t.data_ptr(),
             None if stats_t is None else stats_t.data_ptr(),
             None if stream is None else stream.cuda_stream), (AHPP_ENOTCONVERGED,))
+
+    def query_dense_noalloc(self, q, eps, out_t, stream=None) -> int:
+        """Dense reserves into the caller's device tensor out_t[n_u] with no
+        device allocation (the query state lives in the library's static
+        scratch array)."""
+        return _check(lib().ahpp_query_dense_noalloc(
+            self._h, q, eps, out_t.data_ptr(), None if stream is None else stream.cuda_stream),
+            (AHPP_ENOTCONVERGED,))
 
     def autotune(self, q_sample, eps: float) -> dict:
         q = np.ascontiguousarray(q_sample, np.uint32)

@@ -97,6 +97,10 @@ int ensure(ahpp_graph* g, IoBuf& b, size_t bytes) {
 
 }  // namespace
 
+Q1Params noalloc_params(const ahpp_graph* g, uint32_t q_new, double eps) {
+  return q1_params(g, q_new, eps);
+}
+
 int run_query1_launch(ahpp_graph* g, uint32_t q_new, double eps, cudaStream_t stream) {
   Q1Params p = q1_params(g, q_new, eps);
   AHPP_CUDA(cudaMemsetAsync(g->q1.bar, 0, sizeof(GridBarrier), stream));
