@@ -52,6 +52,12 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--graph", default="medium", choices=["medium", "tiny"])
+    ap.add_argument("--serve-seconds", type=float, default=12.0,
+                    help="open-loop serving window (0 disables the serving measurement)")
+    ap.add_argument("--serve-load", type=float, default=0.8,
+                    help="Poisson arrival rate as a fraction of the measured batched capacity")
+    ap.add_argument("--serve-slots", type=int, default=256)
+    ap.add_argument("--serve-rounds", type=int, default=4)
     return ap.parse_args()
 
 
@@ -282,10 +288,9 @@ def run_ours(args, rank, world, local_rank):
     launch_ms = [a.elapsed_time(b) for a, b in ev]
     dev_s = sum(launch_ms) / 1e3
     st = stats_t.cpu().numpy().view(np.uint8)
-    stats = np.frombuffer(st.tobytes(), dtype=np.dtype([
-        ("rounds", "u4"), ("switch_round", "u4"), ("dense_rounds", "u4"), ("status", "u4"),
-        ("pushes", "u8"), ("n_p", "u8"), ("resid_sum", "f8"), ("reserve_sum", "f8"),
-        ("mass_err", "f8"), ("max_resid", "f8"), ("lambda", "f8"), ("eps_f", "f8")]))
+    ctype_to_np = {"c_uint": "u4", "c_ulong": "u8", "c_double": "f8", "c_int": "i4"}
+    stats = np.frombuffer(st.tobytes(), dtype=np.dtype(
+        [(f.rstrip("_"), ctype_to_np[t.__name__]) for f, t in ahpp.Stats._fields_]))
     rounds = stats["rounds"].astype(np.int64)
     tile = int(info["batch_tile"])
     tile_rounds = int(sum(rounds[i:i + tile].max() for i in range(0, B, tile)))
@@ -339,6 +344,11 @@ def run_ours(args, rank, world, local_rank):
                  "p99_ms": float(np.percentile(lat, 99)), "queries": len(lat),
                  "rounds_example": int(G.query(int(pq[1]), args.eps, 1).stats["rounds"])}
 
+    # serving: open-loop Poisson arrivals on the same graph (continuous batching)
+    served = None
+    if rank == 0 and args.serve_seconds > 0:
+        served = run_serving(ahpp, G, g, args, rate=args.serve_load * value / world)
+
     # roofline of the dominant kernel (the batched persistent launch)
     peak, peak_kind = measured_peak()
     alg = tile_rounds * round_bytes(info, tile) + topk_bytes(info, B)   # one launch (last step)
@@ -371,6 +381,8 @@ def run_ours(args, rank, world, local_rank):
         "latency_note": "batched: a query completes with its 1,024-query step",
         "plain": plain,
         "speedup_vs_plain": (value / world / plain["qps"]) if plain else None,
+        "served": served,
+        "served_speedup_vs_plain": (served["qps"] / plain["qps"]) if (plain and served) else None,
         "rounds_mean": float(rounds.mean()),
         "rounds_max": int(rounds.max()),
         "not_converged": int((stats["status"] != 0).sum()),
@@ -384,6 +396,38 @@ def run_ours(args, rank, world, local_rank):
     }
     G.close()
     return out
+
+
+def run_serving(ahpp, G, g, args, rate):
+    """Submit an open-loop Poisson stream at `rate` queries/s for
+    args.serve_seconds; report completed queries/s and submit-to-result
+    latency percentiles (measured by the server)."""
+    n = max(32, int(rate * args.serve_seconds))
+    t_arr, q, _, _ = synth.draw_stream(n, rate, g.n_u, seed=101)
+    srv = ahpp.Server(G, max_slots=args.serve_slots, rounds_per_step=args.serve_rounds)
+    try:
+        warm = [srv.submit(int(x), args.eps, args.k) for x in q[:8]]
+        for t in warm:
+            srv.wait(t, args.k)
+        tickets = []
+        t0 = time.perf_counter()
+        for i in range(n):
+            delay = t0 + t_arr[i] - time.perf_counter()
+            if delay > 0:
+                time.sleep(delay)
+            tickets.append(srv.submit(int(q[i]), args.eps, args.k))
+        lat = []
+        for t in tickets:
+            r = srv.wait(t, args.k)
+            lat.append(r.stats["served_ms"])
+        span = time.perf_counter() - t0
+        info = srv.info()
+    finally:
+        srv.stop()
+    return {"rate_qps": rate, "queries": n, "qps": n / span, "p50_ms": statistics.median(lat),
+            "p99_ms": float(np.percentile(lat, 99)), "slots": info["slots"],
+            "rounds_per_step": args.serve_rounds, "steps": info["steps"],
+            "note": "open-loop Poisson arrivals at the given rate; qps = completed / (last result - first submit)"}
 
 
 def run_reference(args, rank, world):

@@ -99,6 +99,7 @@ typedef struct {
     double max_resid;          /* max_u r(u) at exit */
     double lambda;             /* lambda used (ASRP) */
     double eps_f;              /* eps / lambda (ASRP) or r_max (APP) */
+    double served_ms;          /* serving: submit-to-completion time in ms (0 otherwise) */
 } ahpp_stats;
 
 typedef struct {
@@ -115,9 +116,11 @@ typedef struct {
 
 /* Serving options. */
 typedef struct {
-    uint32_t max_slots;        /* concurrent queries on the device; 0: from the HBM budget */
+    uint32_t max_slots;        /* concurrent queries on the device (rounded up to whole tiles);
+                                  0: what hbm_budget_bytes leaves after the graph, else 256 */
     uint32_t queue_capacity;   /* pending requests before AHPP_EBUSY; 0: 65536 */
-    uint32_t tile;             /* queries per tile (32 or 64); 0: graph default */
+    uint32_t tile;             /* queries per tile; 0 or the library's tile width */
+    uint32_t rounds_per_step;  /* push rounds per device step between admissions; 0: 4 */
 } ahpp_server_opts;
 
 /* Fill *cfg with the defaults listed above. */
@@ -233,7 +236,8 @@ typedef struct {
 } ahpp_server_info;
 int ahpp_server_info_get(ahpp_server *s, ahpp_server_info *info);
 
-/* Stop the loop, drop queued requests, release the slots.  Safe on NULL. */
+/* Stop the loop, drop queued requests, release the slots and the server.
+ * Safe on NULL.  No other call on s may run concurrently or follow. */
 int ahpp_server_stop(ahpp_server *s);
 
 #ifdef __cplusplus

@@ -52,7 +52,8 @@ class Stats(ctypes.Structure):
                 ("pushes", ctypes.c_uint64), ("n_p", ctypes.c_uint64),
                 ("resid_sum", ctypes.c_double), ("reserve_sum", ctypes.c_double),
                 ("mass_err", ctypes.c_double), ("max_resid", ctypes.c_double),
-                ("lambda_", ctypes.c_double), ("eps_f", ctypes.c_double)]
+                ("lambda_", ctypes.c_double), ("eps_f", ctypes.c_double),
+                ("served_ms", ctypes.c_double)]
 
     def as_dict(self) -> dict:
         return {k.rstrip("_"): getattr(self, k) for k, _ in self._fields_}
@@ -69,7 +70,7 @@ class GraphInfo(ctypes.Structure):
 
 class ServerOpts(ctypes.Structure):
     _fields_ = [("max_slots", ctypes.c_uint32), ("queue_capacity", ctypes.c_uint32),
-                ("tile", ctypes.c_uint32)]
+                ("tile", ctypes.c_uint32), ("rounds_per_step", ctypes.c_uint32)]
 
 
 class ServerInfo(ctypes.Structure):
@@ -300,9 +301,10 @@ STATS_BYTES = ctypes.sizeof(Stats)
 class Server:
     """Continuous-batching server over a loaded graph."""
 
-    def __init__(self, graph: Graph, max_slots: int = 0, queue_capacity: int = 0, tile: int = 0):
+    def __init__(self, graph: Graph, max_slots: int = 0, queue_capacity: int = 0, tile: int = 0,
+                 rounds_per_step: int = 0):
         self.graph = graph
-        o = ServerOpts(max_slots, queue_capacity, tile)
+        o = ServerOpts(max_slots, queue_capacity, tile, rounds_per_step)
         h = _vp()
         _check(lib().ahpp_server_start(graph.handle, ctypes.byref(o), ctypes.byref(h)))
         self._h = h

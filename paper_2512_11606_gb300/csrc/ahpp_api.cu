@@ -44,6 +44,7 @@ __global__ void k_ctl_to_stats(const QCtl* ctl, const unsigned int* maxr, double
   S.max_resid = (double)__uint_as_float(maxr[0]);
   S.lambda = lambda;
   S.eps_f = eps_f;
+  S.served_ms = 0.0;
   *st = S;
 }
 
@@ -416,6 +417,7 @@ static int finish_single(ahpp_graph* g, double eps, ahpp_stats* st) {
     st->max_resid = m;
     st->lambda = g->lambda;
     st->eps_f = eps_f_of(g, eps);
+    st->served_ms = 0.0;
   }
   return status_code(ctl.status);
 }

@@ -78,13 +78,6 @@ static_assert(kTile == 16 || kTile == 32, "tile of 16 or 32 queries");
 #define AHPP_BATCH_MINB 3         // resident blocks per SM the register budget targets
 #endif
 
-struct LaneCtl {
-  double eps_f;
-  unsigned long long n_p, pushes;
-  uint32_t rounds, switch_round;
-  int phase, status, active, valid;
-};
-
 // Smallest float f with (r > th) <=> (r >= f) for every float r: the mark
 // test r > th of Algorithm 4 taken exactly against the FP64 threshold.
 __device__ __forceinline__ float threshold_up(double th) {
@@ -430,10 +423,15 @@ __device__ __forceinline__ unsigned long long score_key(float score, uint32_t ca
 
 }  // namespace
 
-template <typename WA>
+// One persistent cooperative kernel for both batched queries (SERVE = false:
+// n queries packed into tiles, each tile run to completion) and serving steps
+// (SERVE = true: every lane of a tile is a slot; NEW slots are admitted into
+// tiles already in flight, each live tile advances rounds_per_step rounds,
+// slots that finish are finalised and their top-k extracted).
+template <typename WA, bool SERVE>
 __global__ void __launch_bounds__(kThreads, AHPP_BATCH_MINB)
-k_batch(const __grid_constant__ DevGraph g, const __grid_constant__ BatchState st,
-        const __grid_constant__ BatchParams p) {
+k_tiles(const __grid_constant__ DevGraph g, const __grid_constant__ BatchState st,
+        const __grid_constant__ BatchParams p, const __grid_constant__ ServeParams sv) {
   extern __shared__ unsigned char smem[];
   // Per-query control of the current tile, one entry per lane / query.  Warp 0
   // of every block makes the decisions (all blocks read the same round
@@ -441,68 +439,109 @@ k_batch(const __grid_constant__ DevGraph g, const __grid_constant__ BatchState s
   __shared__ LaneCtl s_ctl[kTile];
   __shared__ unsigned long long s_mdeg[kTile];
   __shared__ int s_switch[kTile];
+  __shared__ int s_new[kTile];       // serving: slot admitted at this step
+  __shared__ int s_fin[kTile];       // lane finished: finalise and select top-k
+  __shared__ uint32_t s_k[kTile];    // top-k size of the lane
   __shared__ int s_flag;
-  const uint32_t groups = p.groups;
+  __shared__ TileBuf s_tb;
+  const uint32_t groups = SERVE ? 1u : p.groups;
   const uint32_t nbg = gridDim.x / groups;              // blocks per group
   const uint32_t grp = blockIdx.x / nbg;
   if (grp >= groups) return;                            // leftover blocks
   const uint32_t bid = blockIdx.x - grp * nbg;          // block id within the group
-  const TileBuf& tb = st.tb[grp];
+  const TileBuf& tb = s_tb;
   BCtx c{g, tb, p, (bid * kThreads + threadIdx.x) >> 5, (nbg * kThreads) >> 5,
          bid * kThreads + threadIdx.x, nbg * kThreads, threadIdx.x & 31u};
   const uint32_t lane = c.lane;
   const bool lq = lane < (uint32_t)kTile;               // this lane stands for a query
   const bool warp0 = threadIdx.x < 32;
   const bool app = p.algo == kAlgoAPP;
-  const uint32_t n_tiles = (p.n + kTile - 1) / kTile;
+  const uint32_t n_work = SERVE ? sv.n_live : (p.n + kTile - 1) / kTile;
   const uint32_t n_split = g.b_v.n_split + g.b_a.n_split + g.b_u.n_split;
   const size_t nu32 = (size_t)g.n_u * kTile;
+  const uint32_t kmax = p.kmax;
 
-  for (uint32_t tile = grp; tile < n_tiles; tile += groups) {
-    // ---- init the tile (Algorithm 3 lines 1-2 for every lane)
-    for (size_t i = c.gt; i < nu32; i += c.nt) { tb.r_u[i] = 0.f; tb.pi[i] = 0.f; tb.pic[i] = 0.f; }
-    for (size_t i = c.gt; i < (size_t)g.n_v * kTile; i += c.nt) tb.t_v[i] = 0.f;
-    for (size_t i = c.gt; i < (size_t)g.n_a * kTile; i += c.nt) tb.t_a[i] = 0.f;
-    for (size_t i = c.gt; i < (size_t)n_split * kTile; i += c.nt) tb.split_acc[i] = 0.f;
-    for (size_t i = c.gt; i < n_split; i += c.nt) tb.split_cnt[i] = 0;
-    for (size_t i = c.gt; i < (size_t)kRadixPasses * kTile * kRadixBins; i += c.nt) tb.hist[i] = 0;
-    if (c.gt < 5 * kTile) tb.racc[c.gt] = RAcc{};
-    if (c.gt < kTile) tb.cand_cnt[c.gt] = 0;
-    if (!grid_sync(tb.bar, nbg)) return;
+  for (uint32_t w = grp; w < n_work; w += groups) {
+    const uint32_t tile = SERVE ? sv.live[w] : w;
+    if (threadIdx.x == 0) s_tb = SERVE ? sv.tbufs[tile] : st.tb[grp];
+    __syncthreads();
+    const uint32_t qi = tile * kTile + lane;            // query (batch) or slot (serve) index
+    uint32_t tround = SERVE ? sv.tile_round[tile] : 0u;
 
-    const uint32_t qi = tile * kTile + lane;
-    const bool in_range = lq && qi < p.n;
+    // ---- admission: Algorithm 3 lines 1-2 for every new lane
+    if (!SERVE) {
+      for (size_t i = c.gt; i < nu32; i += c.nt) { tb.r_u[i] = 0.f; tb.pi[i] = 0.f; tb.pic[i] = 0.f; }
+      for (size_t i = c.gt; i < (size_t)g.n_v * kTile; i += c.nt) tb.t_v[i] = 0.f;
+      for (size_t i = c.gt; i < (size_t)g.n_a * kTile; i += c.nt) tb.t_a[i] = 0.f;
+      for (size_t i = c.gt; i < (size_t)n_split * kTile; i += c.nt) tb.split_acc[i] = 0.f;
+      for (size_t i = c.gt; i < n_split; i += c.nt) tb.split_cnt[i] = 0;
+      if (c.gt < 5 * kTile) tb.racc[c.gt] = RAcc{};
+    }
     if (warp0) {
-      // ids and eps come from device memory: an invalid one disables its lane
-      const bool bad = in_range && (p.q[qi] >= g.n_u || !(p.eps[qi] > 0.0));
-      LaneCtl L{0.0, 0, 0, 0, 0, kPhaseAsync, bad ? kStatusBadArg : kStatusOk, 0, 0};
-      if (in_range && !bad) {
-        const uint32_t q_new = p.u_old2new[p.q[qi]];
-        const double eps = p.eps[qi];
-        L.eps_f = app ? eps / (double)p.e_tot : eps / p.lambda;
-        L.active = 1;
-        L.valid = 1;
-        if (bid == 0) {
-          const uint32_t cnt = (g.uv_off[q_new + 1] - g.uv_off[q_new]) + (g.ua_off[q_new + 1] - g.ua_off[q_new]);
-          const double th = app ? L.eps_f * (double)cnt : L.eps_f;
-          RAcc* a0 = &tb.racc[2 * kTile + lane];
-          if (1.0 > th) {
-            tb.r_u[(size_t)q_new * kTile + lane] = -1.f;
-            a0->marked = 1;
-            a0->marked_deg = cnt;
-          } else {
-            tb.r_u[(size_t)q_new * kTile + lane] = 1.f;
-          }
+      LaneCtl L{0.0, 0, 0, 0, 0, kPhaseAsync, kStatusOk, 0, 0};
+      int is_new = 0;
+      uint32_t kk = 0;
+      if (!SERVE) {
+        const bool in_range = lq && qi < p.n;
+        const bool bad = in_range && (p.q[qi] >= g.n_u || !(p.eps[qi] > 0.0));
+        if (bad) L.status = kStatusBadArg;
+        if (in_range && !bad) {
+          L.eps_f = app ? p.eps[qi] / (double)p.e_tot : p.eps[qi] / p.lambda;
+          L.active = 1;
+          L.valid = 1;
+          is_new = 1;
+          kk = kmax ? min(min(p.k[qi], kmax), g.n_u) : 0u;
+        }
+      } else if (lq) {
+        const SlotState& S = sv.slots[qi];
+        kk = S.k;
+        if (S.state == kSlotNew) {
+          L.eps_f = S.eps_f;
+          L.active = 1;
+          L.valid = 1;
+          is_new = 1;
+        } else if (S.state == kSlotRunning) {
+          L = S.ctl;
         }
       }
-      if (lq) s_ctl[lane] = L;
+      if (lq) { s_ctl[lane] = L; s_new[lane] = is_new; s_k[lane] = kk; s_fin[lane] = 0; }
+      const int any = __any_sync(kFull, is_new);
+      if (lane == 0) s_flag = any;
+    }
+    __syncthreads();
+    if (SERVE && s_flag) {
+      // clear the new lanes' columns (the other lanes keep running)
+      const bool nw = lq && s_new[lane];
+      for (size_t u = c.gw; nw && u < g.n_u; u += c.nw) {
+        const size_t i = u * kTile + lane;
+        tb.r_u[i] = 0.f; tb.pi[i] = 0.f; tb.pic[i] = 0.f;
+      }
+      if (bid == 0 && nw) {
+        for (int r = 0; r < 5; ++r) tb.racc[r * kTile + lane] = RAcc{};
+      }
+    }
+    if (!grid_sync(tb.bar, nbg)) return;
+    if (bid == 0 && warp0 && lq && s_new[lane]) {
+      const uint32_t q_new = SERVE ? sv.slots[qi].q_new : p.u_old2new[p.q[qi]];
+      const uint32_t cnt = (g.uv_off[q_new + 1] - g.uv_off[q_new]) + (g.ua_off[q_new + 1] - g.ua_off[q_new]);
+      const double th = app ? s_ctl[lane].eps_f * (double)cnt : s_ctl[lane].eps_f;
+      RAcc* a0 = &tb.racc[((tround + 2) % 3) * kTile + lane];
+      *a0 = RAcc{};
+      if (1.0 > th) {
+        tb.r_u[(size_t)q_new * kTile + lane] = -1.f;
+        a0->marked = 1;
+        a0->marked_deg = cnt;
+      } else {
+        tb.r_u[(size_t)q_new * kTile + lane] = 1.f;
+      }
     }
     if (!grid_sync(tb.bar, nbg)) return;
 
+    // ---- rounds (Algorithm 3 / 4) for the active lanes
     Partials part;
-    uint32_t tround = 0;
     bool wait_fail = false;
-    for (;;) {
+    const uint32_t max_r = SERVE ? sv.rounds_per_step : 0xffffffffu;
+    for (uint32_t done_r = 0;; ++done_r) {
       RAcc* A = &tb.racc[(tround % 3) * kTile];
       const RAcc* P = &tb.racc[((tround + 2) % 3) * kTile];
       if (warp0) {
@@ -511,13 +550,13 @@ k_batch(const __grid_constant__ DevGraph g, const __grid_constant__ BatchState s
           L = s_ctl[lane];
           const uint32_t marked = __ldcg(&P[lane].marked);
           s_mdeg[lane] = __ldcg(&P[lane].marked_deg);
-          if (L.active && (L.phase == kPhaseDone || marked == 0)) { L.phase = kPhaseDone; L.active = 0; }
-          if (L.active && L.rounds >= p.max_rounds) { L.status = kStatusCap; L.active = 0; }
-          if (L.active) L.pushes += marked;
+          if (L.active && (L.phase == kPhaseDone || marked == 0)) { L.phase = kPhaseDone; L.active = 0; s_fin[lane] = 1; }
+          if (L.active && L.rounds >= p.max_rounds) { L.status = kStatusCap; L.active = 0; s_fin[lane] = 1; }
+          if (L.active && done_r < max_r) L.pushes += marked;
           s_ctl[lane] = L;
         }
         const int any = __any_sync(kFull, L.active);
-        if (lane == 0) s_flag = any;
+        if (lane == 0) s_flag = any && done_r < max_r;
       }
       __syncthreads();
       if (!s_flag) break;
@@ -541,6 +580,7 @@ k_batch(const __grid_constant__ DevGraph g, const __grid_constant__ BatchState s
             if ((double)M <= L.eps_f) {
               L.phase = kPhaseDone;
               L.active = 0;
+              s_fin[lane] = 1;
             } else if (L.phase == kPhaseAsync && (double)L.n_p >= bbudget(p, L.eps_f, (double)M)) {
               L.phase = kPhaseSync;
               L.switch_round = L.rounds + 1;
@@ -572,161 +612,213 @@ k_batch(const __grid_constant__ DevGraph g, const __grid_constant__ BatchState s
         if (!grid_sync(tb.bar, nbg)) { wait_fail = true; break; }
       }
     }
-    if (wait_fail && warp0 && lq) s_ctl[lane].status = kStatusWait;
+    if (wait_fail && warp0 && lq && s_ctl[lane].valid) {
+      s_ctl[lane].status = kStatusWait;
+      s_ctl[lane].active = 0;
+      s_fin[lane] = 1;
+    }
     __syncthreads();
-    const bool valid = lq && s_ctl[lane].valid != 0;
+    const bool fin = lq && s_fin[lane] && s_ctl[lane].valid;
+    const uint32_t kq = fin ? s_k[lane] : 0u;
+    int any_fin = 0;
+    for (int l = 0; l < kTile; ++l) any_fin |= s_fin[l];
 
-    // ---- reserves = pi - compensation; per-query sums; dense output
-    {
-      Partials pr, pp;
-      for (size_t u = c.gw; lq && u < g.n_u; u += c.nw) {
-        const size_t i = u * kTile + lane;
-        const float v = fmaxf(tb.pi[i] - tb.pic[i], 0.f);
-        tb.pi[i] = v;
-        const float r = fabsf(tb.r_u[i]);
-        pr.sum_r += (double)r;
-        pr.max_r = fmaxf(pr.max_r, r);
-        pp.sum_r += (double)v;
-        if (valid && p.out_dense) p.out_dense[(size_t)qi * g.n_u + p.u_new2old[u]] = v;
-      }
-      flush_lane_partials(pr, &tb.racc[3 * kTile]);   // residues: sum and max
-      flush_lane_partials(pp, &tb.racc[4 * kTile]);   // reserves: sum
-    }
-    if (!grid_sync(tb.bar, nbg)) return;
-
-    const uint32_t kq = (valid && p.kmax) ? min(min(p.k[qi], p.kmax), g.n_u) : 0u;
-    if (bid == 0 && threadIdx.x < kTile && in_range && p.out_stats) {
-      const LaneCtl L = s_ctl[lane];
-      ahpp_stats S;
-      S.rounds = L.rounds;
-      S.switch_round = L.switch_round;
-      S.dense_rounds = L.rounds;
-      S.status = (uint32_t)((L.status == kStatusOk && L.phase != kPhaseDone && L.valid) ? kStatusCap
-                                                                                     : L.status);
-      S.pushes = L.pushes;
-      S.n_p = L.n_p;
-      S.reserve_sum = __ldcg(&tb.racc[4 * kTile + lane].sum_r);
-      S.resid_sum = __ldcg(&tb.racc[3 * kTile + lane].sum_r);
-      S.mass_err = fabs(S.reserve_sum + S.resid_sum - 1.0);
-      S.max_resid = (double)__uint_as_float(__ldcg(&tb.racc[3 * kTile + lane].max_r_bits));
-      S.lambda = p.lambda;
-      S.eps_f = L.eps_f;
-      p.out_stats[qi] = S;
-    }
-
-    // ---- top-k per lane: radix select over 64-bit (score, ~caller id) keys
-    if (p.kmax) {
-      unsigned int* sh = reinterpret_cast<unsigned int*>(smem);    // [kTile][kRadixBins]
-      unsigned long long prefix = 0;
-      uint32_t krem = kq;
-      for (int pass = 0; pass < kRadixPasses; ++pass) {
-        const int shift = 64 - kRadixBits * (pass + 1);
-        for (int i = threadIdx.x; i < kTile * kRadixBins; i += kThreads) sh[i] = 0;
-        __syncthreads();
-        if (krem && lq) {
-          for (size_t u = c.gw; u < g.n_u; u += c.nw) {
-            const unsigned long long key = score_key(tb.pi[u * kTile + lane], p.u_new2old[u]);
-            if (pass == 0 || (key >> (shift + kRadixBits)) == prefix)
-              atomicAdd(&sh[lane * kRadixBins + ((key >> shift) & (kRadixBins - 1))], 1u);
-          }
+    if (any_fin) {
+      // ---- reserves = pi - compensation; per-query sums; dense output
+      {
+        Partials pr, pp;
+        for (size_t u = c.gw; fin && u < g.n_u; u += c.nw) {
+          const size_t i = u * kTile + lane;
+          const float v = fmaxf(tb.pi[i] - tb.pic[i], 0.f);
+          tb.pi[i] = v;
+          const float r = fabsf(tb.r_u[i]);
+          pr.sum_r += (double)r;
+          pr.max_r = fmaxf(pr.max_r, r);
+          pp.sum_r += (double)v;
+          if (!SERVE && p.out_dense) p.out_dense[(size_t)qi * g.n_u + p.u_new2old[u]] = v;
         }
-        __syncthreads();
-        unsigned int* gh = tb.hist + (size_t)pass * kTile * kRadixBins;
-        for (int i = threadIdx.x; i < kTile * kRadixBins; i += kThreads)
-          if (sh[i]) atomicAdd(&gh[i], sh[i]);
-        if (!grid_sync(tb.bar, nbg)) return;
-        if (krem && lq) {
-          uint32_t cum = 0;
-          int d = kRadixBins - 1;
-          for (; d > 0; --d) {
-            const uint32_t h = __ldcg(&gh[lane * kRadixBins + d]);
-            if (cum + h >= krem) break;
-            cum += h;
-          }
-          krem -= cum;
-          prefix = (prefix << kRadixBits) | (unsigned long long)d;
-        }
-      }
-      // prefix is the exact key of the kq-th largest; keys are distinct
-      if (kq && lq) {
-        for (size_t u = c.gw; u < g.n_u; u += c.nw) {
-          const unsigned long long key = score_key(tb.pi[u * kTile + lane], p.u_new2old[u]);
-          if (key >= prefix) {
-            const uint32_t pos = atomicAdd(&tb.cand_cnt[lane], 1u);
-            if (pos < p.kmax) tb.cand[(size_t)lane * p.kmax + pos] = key;
-          }
-        }
+        flush_lane_partials(pr, &tb.racc[3 * kTile]);   // residues: sum and max
+        flush_lane_partials(pp, &tb.racc[4 * kTile]);   // reserves: sum
+        for (size_t i = c.gt; i < (size_t)kRadixPasses * kTile * kRadixBins; i += c.nt) tb.hist[i] = 0;
+        if (c.gt < kTile) tb.cand_cnt[c.gt] = 0;
       }
       if (!grid_sync(tb.bar, nbg)) return;
-      // sort each lane's keys descending (bitonic in shared memory), one block per lane
-      unsigned long long* sk = reinterpret_cast<unsigned long long*>(smem);
-      for (uint32_t l = bid; l < kTile; l += nbg) {
-        const uint32_t ql = tile * kTile + l;
-        if (ql >= p.n) continue;
-        const bool okl = p.q[ql] < g.n_u && p.eps[ql] > 0.0;
-        const uint32_t kl = okl ? min(min(p.k[ql], p.kmax), g.n_u) : 0u;
-        uint32_t m = 1;
-        while (m < kl) m <<= 1;
-        for (uint32_t i = threadIdx.x; i < m; i += kThreads)
-          sk[i] = i < kl ? tb.cand[(size_t)l * p.kmax + i] : 0ull;
-        __syncthreads();
-        for (uint32_t size = 2; size <= m; size <<= 1) {
-          for (uint32_t stride = size >> 1; stride > 0; stride >>= 1) {
-            for (uint32_t i = threadIdx.x; i < m; i += kThreads) {
-              const uint32_t j = i ^ stride;
-              if (j > i) {
-                const bool desc = (i & size) == 0;
-                const unsigned long long a = sk[i], b = sk[j];
-                if (desc ? (a < b) : (a > b)) { sk[i] = b; sk[j] = a; }
-              }
+
+      if (bid == 0 && fin) {
+        const LaneCtl L = s_ctl[lane];
+        ahpp_stats S;
+        S.rounds = L.rounds;
+        S.switch_round = L.switch_round;
+        S.dense_rounds = L.rounds;
+        S.status = (uint32_t)((L.status == kStatusOk && L.phase != kPhaseDone) ? kStatusCap : L.status);
+        S.pushes = L.pushes;
+        S.n_p = L.n_p;
+        S.reserve_sum = __ldcg(&tb.racc[4 * kTile + lane].sum_r);
+        S.resid_sum = __ldcg(&tb.racc[3 * kTile + lane].sum_r);
+        S.mass_err = fabs(S.reserve_sum + S.resid_sum - 1.0);
+        S.max_resid = (double)__uint_as_float(__ldcg(&tb.racc[3 * kTile + lane].max_r_bits));
+        S.lambda = p.lambda;
+        S.eps_f = L.eps_f;
+        S.served_ms = 0.0;
+        if (p.out_stats) p.out_stats[qi] = S;
+      }
+
+      // ---- top-k per lane: radix select over 64-bit (score, ~caller id) keys
+      if (kmax) {
+        unsigned int* sh = reinterpret_cast<unsigned int*>(smem);    // [kTile][kRadixBins]
+        unsigned long long prefix = 0;
+        uint32_t krem = kq;
+        for (int pass = 0; pass < kRadixPasses; ++pass) {
+          const int shift = 64 - kRadixBits * (pass + 1);
+          for (int i = threadIdx.x; i < kTile * kRadixBins; i += kThreads) sh[i] = 0;
+          __syncthreads();
+          if (krem) {
+            for (size_t u = c.gw; u < g.n_u; u += c.nw) {
+              const unsigned long long key = score_key(tb.pi[u * kTile + lane], p.u_new2old[u]);
+              if (pass == 0 || (key >> (shift + kRadixBits)) == prefix)
+                atomicAdd(&sh[lane * kRadixBins + ((key >> shift) & (kRadixBins - 1))], 1u);
             }
-            __syncthreads();
+          }
+          __syncthreads();
+          unsigned int* gh = tb.hist + (size_t)pass * kTile * kRadixBins;
+          for (int i = threadIdx.x; i < kTile * kRadixBins; i += kThreads)
+            if (sh[i]) atomicAdd(&gh[i], sh[i]);
+          if (!grid_sync(tb.bar, nbg)) return;
+          if (krem) {
+            uint32_t cum = 0;
+            int d = kRadixBins - 1;
+            for (; d > 0; --d) {
+              const uint32_t h = __ldcg(&gh[lane * kRadixBins + d]);
+              if (cum + h >= krem) break;
+              cum += h;
+            }
+            krem -= cum;
+            prefix = (prefix << kRadixBits) | (unsigned long long)d;
           }
         }
-        for (uint32_t i = threadIdx.x; i < kl; i += kThreads) {
-          const unsigned long long key = sk[i];
-          p.out_nodes[(size_t)ql * p.kmax + i] = 0xffffffffu - (uint32_t)(key & 0xffffffffu);
-          p.out_scores[(size_t)ql * p.kmax + i] = __uint_as_float((uint32_t)(key >> 32));
+        // prefix is the exact key of the kq-th largest; keys are distinct
+        if (kq) {
+          for (size_t u = c.gw; u < g.n_u; u += c.nw) {
+            const unsigned long long key = score_key(tb.pi[u * kTile + lane], p.u_new2old[u]);
+            if (key >= prefix) {
+              const uint32_t pos = atomicAdd(&tb.cand_cnt[lane], 1u);
+              if (pos < kmax) tb.cand[(size_t)lane * kmax + pos] = key;
+            }
+          }
         }
-        if (threadIdx.x == 0) p.out_n[ql] = kl;
-        __syncthreads();
+        if (!grid_sync(tb.bar, nbg)) return;
+        // sort each lane's keys descending (bitonic in shared memory), one block per lane
+        unsigned long long* sk = reinterpret_cast<unsigned long long*>(smem);
+        for (uint32_t l = bid; l < kTile; l += nbg) {
+          if (!s_fin[l] || !s_ctl[l].valid) continue;
+          const uint32_t ql = tile * kTile + l;
+          const uint32_t kl = s_k[l];
+          uint32_t m = 1;
+          while (m < kl) m <<= 1;
+          for (uint32_t i = threadIdx.x; i < m; i += kThreads)
+            sk[i] = i < kl ? tb.cand[(size_t)l * kmax + i] : 0ull;
+          __syncthreads();
+          for (uint32_t size = 2; size <= m; size <<= 1) {
+            for (uint32_t stride = size >> 1; stride > 0; stride >>= 1) {
+              for (uint32_t i = threadIdx.x; i < m; i += kThreads) {
+                const uint32_t j = i ^ stride;
+                if (j > i) {
+                  const bool desc = (i & size) == 0;
+                  const unsigned long long a = sk[i], b = sk[j];
+                  if (desc ? (a < b) : (a > b)) { sk[i] = b; sk[j] = a; }
+                }
+              }
+              __syncthreads();
+            }
+          }
+          for (uint32_t i = threadIdx.x; i < kl; i += kThreads) {
+            const unsigned long long key = sk[i];
+            p.out_nodes[(size_t)ql * kmax + i] = 0xffffffffu - (uint32_t)(key & 0xffffffffu);
+            p.out_scores[(size_t)ql * kmax + i] = __uint_as_float((uint32_t)(key >> 32));
+          }
+          if (threadIdx.x == 0) p.out_n[ql] = kl;
+          __syncthreads();
+        }
+      } else if (bid == 0 && fin && p.out_n) {
+        p.out_n[qi] = 0;
       }
-    } else if (bid == 0 && threadIdx.x < kTile && valid && p.out_n) {
-      p.out_n[qi] = 0;
+    }
+    // ---- bad arguments (batch): report and produce no result
+    if (!SERVE && bid == 0 && lq && qi < p.n && s_ctl[lane].status == kStatusBadArg) {
+      if (p.out_stats) {
+        ahpp_stats S{};
+        S.status = kStatusBadArg;
+        p.out_stats[qi] = S;
+      }
+      if (p.out_n) p.out_n[qi] = 0;
+    }
+    // ---- serving: persist the slots' control and the tile's round counter
+    if (SERVE && bid == 0 && warp0) {
+      if (lq) {
+        SlotState& S = sv.slots[qi];
+        if (S.state == kSlotNew || S.state == kSlotRunning) {
+          S.ctl = s_ctl[lane];
+          S.state = s_fin[lane] ? kSlotFinished : kSlotRunning;
+        }
+      }
+      if (lane == 0) sv.tile_round[tile] = tround;
     }
     if (!grid_sync(tb.bar, nbg)) return;
   }
 }
 
-template __global__ void k_batch<float>(const __grid_constant__ DevGraph,
-                                        const __grid_constant__ BatchState,
-                                        const __grid_constant__ BatchParams);
-template __global__ void k_batch<__nv_bfloat16>(const __grid_constant__ DevGraph,
-                                                const __grid_constant__ BatchState,
-                                                const __grid_constant__ BatchParams);
+template __global__ void k_tiles<float, false>(const __grid_constant__ DevGraph,
+                                               const __grid_constant__ BatchState,
+                                               const __grid_constant__ BatchParams,
+                                               const __grid_constant__ ServeParams);
+template __global__ void k_tiles<__nv_bfloat16, false>(const __grid_constant__ DevGraph,
+                                                       const __grid_constant__ BatchState,
+                                                       const __grid_constant__ BatchParams,
+                                                       const __grid_constant__ ServeParams);
+template __global__ void k_tiles<float, true>(const __grid_constant__ DevGraph,
+                                              const __grid_constant__ BatchState,
+                                              const __grid_constant__ BatchParams,
+                                              const __grid_constant__ ServeParams);
+template __global__ void k_tiles<__nv_bfloat16, true>(const __grid_constant__ DevGraph,
+                                                      const __grid_constant__ BatchState,
+                                                      const __grid_constant__ BatchParams,
+                                                      const __grid_constant__ ServeParams);
 
 constexpr size_t kBatchSmem = 32 * 1024;   // radix histograms / sort buffer (4096 keys)
 
+namespace {
+const void* tiles_fn(bool bf16, bool serve) {
+  if (serve) return bf16 ? (const void*)k_tiles<__nv_bfloat16, true> : (const void*)k_tiles<float, true>;
+  return bf16 ? (const void*)k_tiles<__nv_bfloat16, false> : (const void*)k_tiles<float, false>;
+}
+}  // namespace
+
 int launch_batch(const DevGraph& g, const BatchState& s, const BatchParams& p, bool bf16,
                  int grid, cudaStream_t stream) {
-  void* args[] = {(void*)&g, (void*)&s, (void*)&p};
-  cudaError_t e;
-  if (bf16)
-    e = cudaLaunchCooperativeKernel((const void*)k_batch<__nv_bfloat16>, dim3(grid),
-                                    dim3(kThreads), args, kBatchSmem, stream);
-  else
-    e = cudaLaunchCooperativeKernel((const void*)k_batch<float>, dim3(grid), dim3(kThreads),
-                                    args, kBatchSmem, stream);
+  ServeParams sv{};
+  void* args[] = {(void*)&g, (void*)&s, (void*)&p, (void*)&sv};
+  cudaError_t e = cudaLaunchCooperativeKernel(tiles_fn(bf16, false), dim3(grid), dim3(kThreads), args,
+                                              kBatchSmem, stream);
+  return e == cudaSuccess ? 0 : (int)e;
+}
+
+int launch_serve_step(const DevGraph& g, const BatchParams& p, const ServeParams& sv, bool bf16,
+                      int grid, cudaStream_t stream) {
+  BatchState s{};
+  void* args[] = {(void*)&g, (void*)&s, (void*)&p, (void*)&sv};
+  cudaError_t e = cudaLaunchCooperativeKernel(tiles_fn(bf16, true), dim3(grid), dim3(kThreads), args,
+                                              kBatchSmem, stream);
   return e == cudaSuccess ? 0 : (int)e;
 }
 
 int batch_max_grid(bool bf16, int sm_count) {
-  int per_sm = 0;
-  cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-      &per_sm, bf16 ? (const void*)k_batch<__nv_bfloat16> : (const void*)k_batch<float>,
-      kThreads, kBatchSmem);
-  if (e != cudaSuccess || per_sm <= 0) return -1;
-  return per_sm * sm_count;
+  int per_sm = 0, per_sm2 = 0;
+  cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, tiles_fn(bf16, false),
+                                                                kThreads, kBatchSmem);
+  cudaError_t e2 = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm2, tiles_fn(bf16, true),
+                                                                 kThreads, kBatchSmem);
+  if (e != cudaSuccess || e2 != cudaSuccess || per_sm <= 0 || per_sm2 <= 0) return -1;
+  return std::min(per_sm, per_sm2) * sm_count;
 }
 
 }  // namespace ahpp

@@ -65,8 +65,42 @@ struct BatchParams {
   uint32_t dense_div = 32;
 };
 
+// Per-query control of one batched lane (kept in shared memory while a tile
+// runs, in the slot table between serving steps).
+struct LaneCtl {
+  double eps_f;
+  unsigned long long n_p, pushes;
+  uint32_t rounds, switch_round;
+  int phase, status, active, valid;
+};
+
+enum : uint32_t { kSlotFree = 0, kSlotNew = 1, kSlotRunning = 2, kSlotFinished = 3 };
+
+// One serving slot (lane qi % kTile of tile qi / kTile).  The host writes
+// eps_f, q_new, k and state = kSlotNew; the step kernel moves it to Running
+// and Finished; the host frees Finished slots after reading the results.
+struct SlotState {
+  LaneCtl ctl;
+  double eps_f;
+  uint32_t q_new;          // internal id of the source
+  uint32_t k;              // top-k size (already clamped)
+  uint32_t state;
+  uint32_t pad;
+};
+
+struct ServeParams {
+  SlotState* slots = nullptr;        // [n_tiles * kTile]
+  const TileBuf* tbufs = nullptr;    // [n_tiles], device array
+  uint32_t* tile_round = nullptr;    // [n_tiles] rounds run by each tile (accumulator rotation)
+  const uint32_t* live = nullptr;    // [n_live] tiles to advance this step
+  uint32_t n_live = 0;
+  uint32_t rounds_per_step = 1;
+};
+
 int launch_batch(const DevGraph& g, const BatchState& s, const BatchParams& p, bool bf16,
                  int grid, cudaStream_t stream);
+int launch_serve_step(const DevGraph& g, const BatchParams& p, const ServeParams& sv, bool bf16,
+                      int grid, cudaStream_t stream);
 int batch_max_grid(bool bf16, int sm_count);
 
 }  // namespace ahpp

@@ -1,0 +1,164 @@
+"""Serving loop (continuous batching) through the C ABI.
+
+Requests of different eps and k arrive while others are on the device; they
+are admitted into free slots of tiles already in flight.  Every result must
+equal the result of the same query alone (within the 1e-6 tolerance of the
+parity tests) and agree with the FP64 oracle.
+"""
+import time
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2512_11606_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+ALPHA, BETA = 0.15, 0.35
+TOL = 1e-6
+
+
+@pytest.fixture(scope="module")
+def ahpp():
+    from paper_2512_11606_gb300 import build
+    build.build()
+    from paper_2512_11606_gb300 import ahpp as mod
+    return mod
+
+
+@pytest.fixture(scope="module")
+def tiny(ahpp):
+    g = synth.make_graph(**synth.TINY)
+    og = oracle.OracleGraph.from_arrays(g)
+    lam, _ = og.lambda_estimate(ALPHA, BETA)
+    G = ahpp.Graph.from_arrays(g, lam=lam, attr_bf16=0)
+    yield dict(g=g, og=og, lam=lam, G=G)
+    G.close()
+
+
+def check_same(res, alone, k):
+    assert res.nodes.shape[0] == k and alone.nodes.shape[0] == k
+    common = len(set(res.nodes.tolist()) & set(alone.nodes.tolist())) / k
+    assert common >= 0.98
+    a = dict(zip(alone.nodes.tolist(), alone.scores.tolist()))
+    for n, s in zip(res.nodes.tolist(), res.scores.tolist()):
+        if n in a:
+            assert abs(s - a[n]) <= TOL
+
+
+def test_served_results_equal_alone_in_a_mix(ahpp, tiny):
+    G, og, lam = tiny["G"], tiny["og"], tiny["lam"]
+    rng = np.random.default_rng(3)
+    n = 90
+    qs = synth.draw_queries(tiny["g"].n_u, n, seed=31)
+    eps = np.exp(rng.uniform(np.log(1e-7), np.log(1e-4), n))
+    ks = rng.choice([10, 50], n)
+    srv = ahpp.Server(G, max_slots=64, rounds_per_step=2)
+    try:
+        # first wave, then more requests while the first ones are in flight
+        tickets = [srv.submit(int(qs[i]), float(eps[i]), int(ks[i])) for i in range(40)]
+        first = srv.wait(tickets[0], int(ks[0]))
+        assert first is not None
+        tickets += [srv.submit(int(qs[i]), float(eps[i]), int(ks[i])) for i in range(40, n)]
+        info = srv.info()
+        assert info["submitted"] == n and info["slots"] == 64
+        results = [first] + [srv.wait(t, int(k)) for t, k in zip(tickets[1:], ks[1:])]
+        info = srv.info()
+        assert info["completed"] == n and info["in_flight"] == 0 and info["queued"] == 0
+        assert info["steps"] >= 2
+    finally:
+        srv.stop()
+    for i in [0, 1, 39, 40, 41, 77, 89]:
+        r = results[i]
+        assert r.rc == 0 and r.stats["status"] == 0
+        alone = G.query(int(qs[i]), float(eps[i]), int(ks[i]))
+        check_same(r, alone, int(ks[i]))
+        assert r.stats["rounds"] == alone.stats["rounds"]
+        ref = og.push("asrp", ALPHA, BETA, int(qs[i]), float(eps[i]), lam=lam)
+        tol = max(TOL, float(eps[i]))
+        assert np.all(np.abs(r.scores - ref.pi[r.nodes]) <= tol)
+
+
+def test_admission_while_in_flight(ahpp, tiny):
+    """Slots free up and are refilled while other slots of the same tile run."""
+    G = tiny["G"]
+    srv = ahpp.Server(G, max_slots=32, rounds_per_step=1)
+    try:
+        qs = synth.draw_queries(tiny["g"].n_u, 64, seed=41)
+        # loose eps finish in a few rounds, tight ones take many: the loose
+        # ones' slots are reused while the tight ones are still running
+        eps = [1e-3 if i % 2 else 1e-8 for i in range(64)]
+        t = [srv.submit(int(q), e, 5) for q, e in zip(qs, eps)]
+        seen_mix = False
+        for _ in range(2000):
+            info = srv.info()
+            if info["completed"] > 0 and info["in_flight"] > 0 and info["completed"] + info["in_flight"] > 32:
+                seen_mix = True
+                break
+            time.sleep(0.001)
+        res = [srv.wait(x, 5) for x in t]
+        assert all(r is not None and r.rc == 0 for r in res)
+        assert seen_mix
+    finally:
+        srv.stop()
+
+
+def test_queue_full_and_bad_requests(ahpp, tiny):
+    G = tiny["G"]
+    srv = ahpp.Server(G, max_slots=32, queue_capacity=2, rounds_per_step=8)
+    try:
+        got, busy = [], 0
+        for q in synth.draw_queries(tiny["g"].n_u, 200, seed=51):
+            t = srv.try_submit(int(q), 1e-8, 10)
+            if t is None:
+                busy += 1
+            else:
+                got.append(t)
+        assert busy > 0 and srv.info()["rejected"] == busy
+        with pytest.raises(ahpp.AhppError) as e:
+            srv.submit(tiny["g"].n_u, 1e-6, 10)
+        assert e.value.code == ahpp.AHPP_EINVAL
+        with pytest.raises(ahpp.AhppError):
+            srv.submit(0, -1.0, 10)
+        for t in got:
+            assert srv.wait(t, 10).rc == 0
+        with pytest.raises(ahpp.AhppError) as e:
+            srv.wait(got[0], 10)          # delivered once
+        assert e.value.code == ahpp.AHPP_EINVAL
+    finally:
+        srv.stop()
+
+
+def test_hbm_budget_limits_slots(ahpp, tiny):
+    g = tiny["g"]
+    G = ahpp.Graph.from_arrays(g, lam=tiny["lam"], attr_bf16=0)
+    info = G.info
+    G.close()
+    used = info["graph_bytes"] + info["query_state_bytes"]
+    per_tile_lower = g.n_u * 32 * 12            # residues, reserves, compensation of one tile
+    room = 12_000_000
+    G = ahpp.Graph.from_arrays(g, lam=tiny["lam"], attr_bf16=0, hbm_budget_bytes=used + room)
+    try:
+        srv = ahpp.Server(G)
+        slots = srv.info()["slots"]
+        srv.stop()
+        assert 32 <= slots and (slots // 32) * per_tile_lower <= room
+    finally:
+        G.close()
+    G = ahpp.Graph.from_arrays(g, lam=tiny["lam"], attr_bf16=0, hbm_budget_bytes=used + 100_000)
+    try:
+        with pytest.raises(ahpp.AhppError) as e:
+            ahpp.Server(G)
+        assert e.value.code == ahpp.AHPP_ENOMEM
+    finally:
+        G.close()
+
+
+def test_served_latency_is_reported(ahpp, tiny):
+    srv = ahpp.Server(tiny["G"], max_slots=32)
+    try:
+        t = srv.submit(5, 1e-6, 10)
+        r = srv.wait(t, 10)
+        assert r.stats["served_ms"] > 0
+    finally:
+        srv.stop()

@@ -39,7 +39,7 @@ def test_every_declared_symbol_is_exported(lib):
 def test_struct_sizes_match_header(lib):
     from paper_2512_11606_gb300 import ahpp
     # field lists mirror include/ahpp.h; sizes follow the C layout rules
-    assert ctypes.sizeof(ahpp.Stats) == 4 * 4 + 8 * 2 + 8 * 6
+    assert ctypes.sizeof(ahpp.Stats) == 4 * 4 + 8 * 2 + 8 * 7
     assert ctypes.sizeof(ahpp.GraphDesc) == 8 * 11
     c = ahpp.default_config()
     assert c.alpha == 0.15 and c.beta == 0.35 and c.algo == ahpp.AHPP_ASRP
