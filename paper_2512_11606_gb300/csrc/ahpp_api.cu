@@ -159,13 +159,14 @@ int ensure_batch(ahpp_graph* g, uint32_t groups, uint32_t kmax) {
       t.pic = (float*)A((size_t)G.n_u * kTile * 4);
       t.t_v = (float*)A((size_t)std::max(G.n_v, 1u) * kTile * 4);
       t.t_a = (float*)A((size_t)std::max(G.n_a, 1u) * kTile * 4);
+      t.t_a2 = (float*)A((size_t)std::max(G.n_a, 1u) * kTile * 4);
       t.split_acc = (float*)A(std::max<size_t>(n_split, 1) * kTile * 4);
       t.split_cnt = (uint32_t*)A(std::max<size_t>(n_split, 1) * 4);
       t.racc = (RAcc*)A(5 * kTile * sizeof(RAcc));
       t.bar = (GridBarrier*)A(sizeof(GridBarrier));
       t.hist = (unsigned int*)A((size_t)kRadixPasses * kTile * kRadixBins * 4);
       t.cand_cnt = (uint32_t*)A(kTile * 4);
-      if (!t.r_u || !t.pi || !t.pic || !t.t_v || !t.t_a || !t.split_acc || !t.split_cnt ||
+      if (!t.r_u || !t.pi || !t.pic || !t.t_v || !t.t_a || !t.t_a2 || !t.split_acc || !t.split_cnt ||
           !t.racc || !t.bar || !t.hist || !t.cand_cnt) {
         set_error("batched state allocation failed");
         return AHPP_ENOMEM;

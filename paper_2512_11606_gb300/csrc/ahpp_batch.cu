@@ -74,6 +74,9 @@ static_assert(kTile == 16 || kTile == 32, "tile of 16 or 32 queries");
 #ifndef AHPP_BATCH_WAVES
 #define AHPP_BATCH_WAVES 1        // 8-entry gather waves issued together (1 or 2)
 #endif
+#ifndef AHPP_ATTR_PUSH
+#define AHPP_ATTR_PUSH 0          // attribute hop pushed from phase 2 (1) or pulled in phase 1 (0)
+#endif
 #ifndef AHPP_BATCH_MINB
 #define AHPP_BATCH_MINB 3         // resident blocks per SM the register budget targets
 #endif
@@ -94,11 +97,41 @@ __device__ __forceinline__ uint64_t policy_keep() {
   asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(pol));
   return pol;
 }
+#ifndef AHPP_GATHER_HINT
+#define AHPP_GATHER_HINT 0        // gathers load with the L2 evict-last policy (measured slower)
+#endif
+#ifndef AHPP_STREAM_HINT
+#define AHPP_STREAM_HINT 1        // graph arrays and reserves are streamed with evict-first loads
+#endif
+template <typename T>
+__device__ __forceinline__ T ld_stream(const T* p) {
+#if AHPP_STREAM_HINT
+  return __ldcs(p);
+#else
+  return *p;
+#endif
+}
+#ifndef AHPP_STORE_HINT
+#define AHPP_STORE_HINT 0         // rows that the next phase gathers are stored evict-last
+#endif
 __device__ __forceinline__ float4 ld_keep4(const float* p, uint64_t pol) {
+#if AHPP_GATHER_HINT
   float4 v;
   asm volatile("ld.global.L2::cache_hint.v4.f32 {%0, %1, %2, %3}, [%4], %5;"
                : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w) : "l"(p), "l"(pol));
   return v;
+#else
+  return *reinterpret_cast<const float4*>(p);
+#endif
+}
+__device__ __forceinline__ void st_keep4(float* p, float4 v) {
+#if AHPP_STORE_HINT
+  const uint64_t pol = policy_keep();
+  asm volatile("st.global.L2::cache_hint.v4.f32 [%0], {%1, %2, %3, %4}, %5;"
+               :: "l"(p), "f"(v.x), "f"(v.y), "f"(v.z), "f"(v.w), "l"(pol) : "memory");
+#else
+  *reinterpret_cast<float4*>(p) = v;
+#endif
 }
 
 __device__ __forceinline__ float4 f4_fma(float c, float4 x, float4 a) {
@@ -242,10 +275,14 @@ __device__ __forceinline__ Unit unit_of(const ItemList& L, uint32_t u, const uin
   return x;
 }
 
-// Phase 1: t_V and t_A of the tile's 32 queries.
+// Phase 1: t_V (and, when do_a, t_A into ta_out) of the tile's 32 queries.
 //   t_V[v] = sum_u c_uv(u,v) p_u;   t_A[a] = k_attr cnorm_a[a] sum_u w(u,a) rnorm_u[u] p_u
+// In a normal round t_A was already pushed by the previous phase 2 into
+// ta_scan: phase 1 then only counts its active attributes (Algorithm 4's n_p)
+// and clears ta_zero, the buffer the coming phase 2 pushes into.
 template <typename WA>
-__device__ __forceinline__ void gphase1(const BCtx& c, RAcc* A) {
+__device__ __forceinline__ void gphase1(const BCtx& c, RAcc* A, bool do_v, bool do_a, float* ta_out,
+                                        const float* ta_scan, float* ta_zero, bool count) {
   const DevGraph& g = c.g;
   const uint32_t lane = c.lane, gl = lane & (kGL - 1), gi = lane / kGL;
   const unsigned gmask = ((1u << kGL) - 1u) << (gi * kGL);
@@ -256,8 +293,20 @@ __device__ __forceinline__ void gphase1(const BCtx& c, RAcc* A) {
     return make_float4(fmaxf(-x.x, 0.f), fmaxf(-x.y, 0.f), fmaxf(-x.z, 0.f), fmaxf(-x.w, 0.f));
   };
   Q4Partials part;
-  const uint32_t nuv = g.b_v.n_items + (g.n_v - g.b_v.n_long);
-  const uint32_t nua = g.b_a.n_items + (g.n_a - g.b_a.n_long);
+  if (ta_scan || ta_zero) {
+    for (uint32_t a = c.gw * kGPW + gi; a < g.n_a; a += c.nw * kGPW) {
+      const size_t i = (size_t)a * kTile + kQL * gl;
+      if (ta_scan) {
+        const float4 t = *reinterpret_cast<const float4*>(ta_scan + i);
+        const uint32_t d = g.au_off[a + 1] - g.au_off[a];
+        part.np[0] += t.x > 0.f ? d : 0; part.np[1] += t.y > 0.f ? d : 0;
+        part.np[2] += t.z > 0.f ? d : 0; part.np[3] += t.w > 0.f ? d : 0;
+      }
+      if (ta_zero) *reinterpret_cast<float4*>(ta_zero + i) = make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+  }
+  const uint32_t nuv = do_v ? g.b_v.n_items + (g.n_v - g.b_v.n_long) : 0u;
+  const uint32_t nua = do_a ? g.b_a.n_items + (g.n_a - g.b_a.n_long) : 0u;
   const uint32_t total = nuv + nua;
   for (uint32_t base = c.gw * kGPW; base < total; base += c.nw * kGPW) {
     const uint32_t uix = base + gi;
@@ -271,11 +320,11 @@ __device__ __forceinline__ void gphase1(const BCtx& c, RAcc* A) {
     // V rows and attribute rows in one warp: both gathers run, each group
     // keeps the one of its own kind (ranges are empty for the other)
     const float4 sv = group_accum(is_a ? 0u : b, is_a ? 0u : e, stages, gl,
-        [&](uint32_t k, uint32_t& i, float& w) { i = __ldcs(g.vu_idx + k); w = __ldcs(g.vu_c + k); }, gp);
+        [&](uint32_t k, uint32_t& i, float& w) { i = ld_stream(g.vu_idx + k); w = ld_stream(g.vu_c + k); }, gp);
     const uint32_t stages_a = warp_max_u32(is_a ? (e - b + 31) / 32 : 0u);
     const float4 sa = group_accum(is_a ? b : 0u, is_a ? e : 0u, stages_a, gl,
         [&](uint32_t k, uint32_t& i, float& w) {
-          i = __ldcs(g.au_idx + k);
+          i = ld_stream(g.au_idx + k);
           w = wload<WA>(g.au_w, k) * g.rnorm_u[i];
         }, gp);
     if (!ok) continue;
@@ -289,35 +338,37 @@ __device__ __forceinline__ void gphase1(const BCtx& c, RAcc* A) {
     }
     const uint32_t R = un.row;
     if (!is_a) {
-      *reinterpret_cast<float4*>(c.t.t_v + (size_t)R * kTile + kQL * gl) = s;
+      st_keep4(c.t.t_v + (size_t)R * kTile + kQL * gl, s);
       const uint32_t d = g.vu_off[R + 1] - g.vu_off[R];
       part.np[0] += s.x > 0.f ? d : 0; part.np[1] += s.y > 0.f ? d : 0;
       part.np[2] += s.z > 0.f ? d : 0; part.np[3] += s.w > 0.f ? d : 0;
     } else {
       const float f = g.k_attr * g.cnorm_a[R];
       const float4 tv = make_float4(f * s.x, f * s.y, f * s.z, f * s.w);
-      *reinterpret_cast<float4*>(c.t.t_a + (size_t)R * kTile + kQL * gl) = tv;
+      *reinterpret_cast<float4*>(ta_out + (size_t)R * kTile + kQL * gl) = tv;
       const uint32_t d = g.au_off[R + 1] - g.au_off[R];
       part.np[0] += tv.x > 0.f ? d : 0; part.np[1] += tv.y > 0.f ? d : 0;
       part.np[2] += tv.z > 0.f ? d : 0; part.np[3] += tv.w > 0.f ? d : 0;
     }
   }
-  flush_q4(part, A);
+  if (count) flush_q4(part, A);
 }
 
 // Residue update of row u for this lane's 4 queries: reserve update of the
 // queries that pushed u this round, then the mark for the next round.
-__device__ __forceinline__ void gepilogue2(const BCtx& c, uint32_t u, float4 s, uint32_t cnt,
-                                           const float* th, const int* act, const LaneCtl* app_ctl,
-                                           Q4Partials& part) {
-  if (!(act[0] | act[1] | act[2] | act[3])) return;
+__device__ __forceinline__ float4 gepilogue2(const BCtx& c, uint32_t u, float4 s, uint32_t cnt,
+                                             const float* th, const int* act, const LaneCtl* app_ctl,
+                                             Q4Partials& part) {
+  float4 pushed = make_float4(0.f, 0.f, 0.f, 0.f);
+  if (!(act[0] | act[1] | act[2] | act[3])) return pushed;
+  float* pp4 = &pushed.x;
   const uint32_t gl = c.lane & (kGL - 1);
   const size_t i = (size_t)u * kTile + kQL * gl;
   float4* rp = reinterpret_cast<float4*>(c.t.r_u + i);
   float4* pp = reinterpret_cast<float4*>(c.t.pi + i);
   float4* cp = reinterpret_cast<float4*>(c.t.pic + i);
   float4 r = *rp;
-  float4 pv = __ldcs(pp), pc = __ldcs(cp);
+  float4 pv = ld_stream(pp), pc = ld_stream(cp);
   float* rr = &r.x;
   float* pvv = &pv.x;
   float* pcc = &pc.x;
@@ -340,19 +391,62 @@ __device__ __forceinline__ void gepilogue2(const BCtx& c, uint32_t u, float4 s, 
                               : r_new >= th[j];
     if (mark) {
       rr[j] = -r_new;
+      pp4[j] = r_new;
       part.marked[j] += 1;
       part.mdeg[j] += cnt;
     } else {
       rr[j] = r_new;
     }
   }
-  *rp = r;
+  st_keep4(c.t.r_u + i, r);
   if (pushed_any) { __stcs(pp, pv); __stcs(cp, pc); }
+  return pushed;
+}
+
+// Attribute hop of the coming round, pushed as soon as u is marked: for every
+// a in A(u), t_A'[a] += k_attr cnorm_a[a] w(u,a) rnorm_u[u] p_u (Eq. 2's two
+// factors and Algorithm 3's U-push share), one float4 atomic per lane and
+// attribute; t_A' is small enough to stay in L2.
+template <typename WA>
+__device__ __forceinline__ void push_attr(const DevGraph& g, uint32_t u, float4 p, float* ta_push,
+                                          uint32_t gl, unsigned gmask) {
+  const bool mine = p.x > 0.f || p.y > 0.f || p.z > 0.f || p.w > 0.f;
+  if (!__any_sync(gmask, mine)) return;               // group-uniform
+  const uint32_t b = g.ua_off[u], e = g.ua_off[u + 1];
+  const float f = g.k_attr * g.rnorm_u[u];
+  for (uint32_t k0 = b; k0 < e; k0 += kGL * kSlots) {
+    // stage up to 32 entries over the group's lanes (coalesced), then every
+    // lane issues one float4 atomic per entry for its 4 queries
+    const uint32_t n = min((uint32_t)(kGL * kSlots), e - k0);
+    uint32_t mi[kSlots];
+    float mc[kSlots];
+#pragma unroll
+    for (int s = 0; s < kSlots; ++s) {
+      const uint32_t j = gl + kGL * s;
+      mi[s] = 0; mc[s] = 0.f;
+      if (j < n) {
+        mi[s] = g.ua_idx[k0 + j];
+        mc[s] = f * wload<WA>(g.ua_w, k0 + j) * g.cnorm_a[mi[s]];
+      }
+    }
+#pragma unroll
+    for (int s = 0; s < kSlots; ++s) {
+#pragma unroll
+      for (int t = 0; t < kGL; ++t) {
+        const uint32_t a = __shfl_sync(gmask, mi[s], t, kGL);
+        const float cf = __shfl_sync(gmask, mc[s], t, kGL);
+        if ((uint32_t)(kGL * s + t) < n && mine)
+          atomicAdd(reinterpret_cast<float4*>(ta_push + (size_t)a * kTile + kQL * gl),
+                    make_float4(cf * p.x, cf * p.y, cf * p.z, cf * p.w));
+      }
+    }
+  }
 }
 
 // Phase 2: new residues of every U node for the tile's 32 queries.
 template <typename WA>
-__device__ __forceinline__ void gphase2(const BCtx& c, const LaneCtl* ctl, RAcc* A) {
+__device__ __forceinline__ void gphase2(const BCtx& c, const LaneCtl* ctl, RAcc* A,
+                                        const float* ta_in, float* ta_push) {
   const DevGraph& g = c.g;
   const uint32_t lane = c.lane, gl = lane & (kGL - 1), gi = lane / kGL;
   const unsigned gmask = ((1u << kGL) - 1u) << (gi * kGL);
@@ -367,7 +461,7 @@ __device__ __forceinline__ void gphase2(const BCtx& c, const LaneCtl* ctl, RAcc*
     th[j] = app ? 0.f : threshold_up(q.phase == kPhaseSync ? 0.0 : q.eps_f);
   }
   const float* __restrict__ t_v = c.t.t_v;
-  const float* __restrict__ t_a = c.t.t_a;
+  const float* __restrict__ t_a = ta_in;
   const uint64_t pol = policy_keep();
   auto gv = [&](uint32_t v) { return ld_keep4(t_v + (size_t)v * kTile + kQL * gl, pol); };
   auto ga = [&](uint32_t a) { return ld_keep4(t_a + (size_t)a * kTile + kQL * gl, pol); };
@@ -393,9 +487,9 @@ __device__ __forceinline__ void gphase2(const BCtx& c, const LaneCtl* ctl, RAcc*
     const uint32_t ab = b2 + (z > dv ? z - dv : 0), ae = b2 + (w > dv ? w - dv : 0);
     const uint32_t sv = warp_max_u32((ve - vb + 31) / 32), sa = warp_max_u32((ae - ab + 31) / 32);
     float4 s = group_accum(vb, ve, sv, gl,
-        [&](uint32_t k, uint32_t& i, float& wt) { i = __ldcs(g.uv_idx + k); wt = __ldcs(g.uv_w + k); }, gv);
+        [&](uint32_t k, uint32_t& i, float& wt) { i = ld_stream(g.uv_idx + k); wt = ld_stream(g.uv_w + k); }, gv);
     const float4 s2 = group_accum(ab, ae, sa, gl,
-        [&](uint32_t k, uint32_t& i, float& wt) { i = __ldcs(g.ua_idx + k); wt = wload<WA>(g.ua_w, k); }, ga);
+        [&](uint32_t k, uint32_t& i, float& wt) { i = ld_stream(g.ua_idx + k); wt = wload<WA>(g.ua_w, k); }, ga);
     if (!ok) continue;
     s = make_float4(s.x + s2.x, s.y + s2.y, s.z + s2.z, s.w + s2.w);
     if (slot != 0xffffffffu) {
@@ -404,7 +498,8 @@ __device__ __forceinline__ void gphase2(const BCtx& c, const LaneCtl* ctl, RAcc*
       if (!split_combine4(c.t, sl, g.b_u.split_nchunks[slot], s, gl, gmask, &tot)) continue;
       s = tot;
     }
-    gepilogue2(c, u, s, dv + da, th, act, app ? ctl : nullptr, part);
+    const float4 pushed = gepilogue2(c, u, s, dv + da, th, act, app ? ctl : nullptr, part);
+    if (ta_push) push_attr<WA>(g, u, pushed, ta_push, gl, gmask);
   }
   flush_q4(part, A);
 }
@@ -472,7 +567,7 @@ k_tiles(const __grid_constant__ DevGraph g, const __grid_constant__ BatchState s
     if (!SERVE) {
       for (size_t i = c.gt; i < nu32; i += c.nt) { tb.r_u[i] = 0.f; tb.pi[i] = 0.f; tb.pic[i] = 0.f; }
       for (size_t i = c.gt; i < (size_t)g.n_v * kTile; i += c.nt) tb.t_v[i] = 0.f;
-      for (size_t i = c.gt; i < (size_t)g.n_a * kTile; i += c.nt) tb.t_a[i] = 0.f;
+      for (size_t i = c.gt; i < (size_t)g.n_a * kTile; i += c.nt) { tb.t_a[i] = 0.f; tb.t_a2[i] = 0.f; }
       for (size_t i = c.gt; i < (size_t)n_split * kTile; i += c.nt) tb.split_acc[i] = 0.f;
       for (size_t i = c.gt; i < n_split; i += c.nt) tb.split_cnt[i] = 0;
       if (c.gt < 5 * kTile) tb.racc[c.gt] = RAcc{};
@@ -516,6 +611,10 @@ k_tiles(const __grid_constant__ DevGraph g, const __grid_constant__ BatchState s
         const size_t i = u * kTile + lane;
         tb.r_u[i] = 0.f; tb.pi[i] = 0.f; tb.pic[i] = 0.f;
       }
+      for (size_t a = c.gw; nw && a < g.n_a; a += c.nw) {
+        tb.t_a[a * kTile + lane] = 0.f;
+        tb.t_a2[a * kTile + lane] = 0.f;
+      }
       if (bid == 0 && nw) {
         for (int r = 0; r < 5; ++r) tb.racc[r * kTile + lane] = RAcc{};
       }
@@ -531,6 +630,13 @@ k_tiles(const __grid_constant__ DevGraph g, const __grid_constant__ BatchState s
         tb.r_u[(size_t)q_new * kTile + lane] = -1.f;
         a0->marked = 1;
         a0->marked_deg = cnt;
+        // the source's attribute push of the first round (see push_attr)
+        float* ta_cur = (tround & 1) ? tb.t_a2 : tb.t_a;
+        const float f = g.k_attr * g.rnorm_u[q_new];
+        for (uint32_t k = g.ua_off[q_new]; AHPP_ATTR_PUSH && k < g.ua_off[q_new + 1]; ++k) {
+          const uint32_t a = g.ua_idx[k];
+          ta_cur[(size_t)a * kTile + lane] += f * wload<WA>(g.ua_w, k) * g.cnorm_a[a];
+        }
       } else {
         tb.r_u[(size_t)q_new * kTile + lane] = 1.f;
       }
@@ -562,9 +668,14 @@ k_tiles(const __grid_constant__ DevGraph g, const __grid_constant__ BatchState s
       if (!s_flag) break;
       if (bid == 0 && threadIdx.x < kTile) tb.racc[((tround + 1) % 3) * kTile + threadIdx.x] = RAcc{};
 
-      gphase1<WA>(c, A);
+      float* ta_cur = (tround & 1) ? tb.t_a2 : tb.t_a;     // t_A of this round
+      float* ta_next = (tround & 1) ? tb.t_a : tb.t_a2;    // t_A of the next round
+      if (AHPP_ATTR_PUSH)
+        gphase1<WA>(c, A, true, false, nullptr, ta_cur, ta_next, true);
+      else
+        gphase1<WA>(c, A, true, true, ta_cur, nullptr, nullptr, true);
       if (!grid_sync(tb.bar, nbg)) { wait_fail = true; break; }
-      gphase2<WA>(c, s_ctl, A);
+      gphase2<WA>(c, s_ctl, A, ta_cur, AHPP_ATTR_PUSH ? ta_next : nullptr);
       if (!grid_sync(tb.bar, nbg)) { wait_fail = true; break; }
       ++tround;
 
@@ -610,6 +721,12 @@ k_tiles(const __grid_constant__ DevGraph g, const __grid_constant__ BatchState s
         }
         flush_lane_partials(part, A);
         if (!grid_sync(tb.bar, nbg)) { wait_fail = true; break; }
+        // the new marks also push into the next round's t_A: recompute it by
+        // the pull form from the complete marks (once per switch)
+        if (AHPP_ATTR_PUSH) {
+          gphase1<WA>(c, A, false, true, (tround & 1) ? tb.t_a2 : tb.t_a, nullptr, nullptr, false);
+          if (!grid_sync(tb.bar, nbg)) { wait_fail = true; break; }
+        }
       }
     }
     if (wait_fail && warp0 && lq && s_ctl[lane].valid) {

@@ -24,6 +24,7 @@ constexpr int kRadixPasses = 64 / kRadixBits;
 struct TileBuf {
   float *r_u = nullptr, *pi = nullptr, *pic = nullptr;   // [n_u][kTile]
   float *t_v = nullptr, *t_a = nullptr;                  // [n_v][kTile], [n_a][kTile]
+  float* t_a2 = nullptr;                                 // second t_A buffer (pushed for the next round)
   float* split_acc = nullptr;                            // [n_split][kTile]
   uint32_t* split_cnt = nullptr;                         // [n_split]
   RAcc* racc = nullptr;                                  // [5][kTile]: 3 rounds + 2 final sums

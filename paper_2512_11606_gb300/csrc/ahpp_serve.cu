@@ -286,6 +286,7 @@ int ahpp_server_start(ahpp_graph* g, const ahpp_server_opts* opts, ahpp_server**
       b.pic = (float*)s->dalloc((size_t)G.n_u * kTile * 4);
       b.t_v = (float*)s->dalloc((size_t)std::max(G.n_v, 1u) * kTile * 4);
       b.t_a = (float*)s->dalloc((size_t)std::max(G.n_a, 1u) * kTile * 4);
+      b.t_a2 = (float*)s->dalloc((size_t)std::max(G.n_a, 1u) * kTile * 4);
       b.split_acc = (float*)s->dalloc(std::max<size_t>(n_split, 1) * kTile * 4);
       b.split_cnt = (uint32_t*)s->dalloc(std::max<size_t>(n_split, 1) * 4);
       b.racc = (RAcc*)s->dalloc(5 * kTile * sizeof(RAcc));
@@ -293,7 +294,7 @@ int ahpp_server_start(ahpp_graph* g, const ahpp_server_opts* opts, ahpp_server**
       b.hist = (unsigned int*)s->dalloc((size_t)kRadixPasses * kTile * kRadixBins * 4);
       b.cand = (unsigned long long*)s->dalloc((size_t)kTile * s->kmax * 8);
       b.cand_cnt = (uint32_t*)s->dalloc(kTile * 4);
-      ok = b.r_u && b.pi && b.pic && b.t_v && b.t_a && b.split_acc && b.split_cnt && b.racc &&
+      ok = b.r_u && b.pi && b.pic && b.t_v && b.t_a && b.t_a2 && b.split_acc && b.split_cnt && b.racc &&
            b.hist && b.cand && b.cand_cnt;
       if (ok) {
         // the split accumulators and counters must start at zero (kept zero by the kernel)
