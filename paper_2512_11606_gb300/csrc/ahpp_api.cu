@@ -145,7 +145,8 @@ int ensure_batch(ahpp_graph* g, uint32_t groups, uint32_t kmax) {
   kmax = std::max<uint32_t>(kmax, 1);
   if (s.n_groups >= groups && s.kmax_cap >= kmax) return AHPP_OK;
   const DevGraph& G = g->dg;
-  const size_t n_split = (size_t)G.b_v.n_split + G.b_a.n_split + G.b_u.n_split;
+  const size_t n_split = std::max((size_t)G.b_v.n_split + G.b_a.n_split + G.b_u.n_split,
+                                  (size_t)G.m_v.n_split + G.m_a.n_split + G.m_u.n_split);
   const uint32_t kcap = std::max(kmax, s.kmax_cap);
   const uint32_t ng = std::max(groups, s.n_groups);
   uint64_t bytes = 0;
@@ -172,6 +173,10 @@ int ensure_batch(ahpp_graph* g, uint32_t groups, uint32_t kmax) {
         return AHPP_ENOMEM;
       }
       AHPP_CUDA(cudaMemset(t.bar, 0, sizeof(GridBarrier)));
+      if (encode_tile_maps(t, G.n_u, G.n_v, G.n_a) != 0) {
+        set_error("batched state: tensor map encoding failed");
+        return AHPP_ECUDA;
+      }
     }
     if (fresh || kcap > s.kmax_cap) {
       t.cand = (unsigned long long*)A((size_t)kTile * kcap * 8);

@@ -10,6 +10,7 @@
 // on the other queries of the tile.  Top-k per query is a per-lane radix
 // select over (score, caller id) keys.
 #include "ahpp_batch.cuh"
+#include "ahpp_tma.cuh"
 
 namespace ahpp {
 
@@ -77,8 +78,14 @@ static_assert(kTile == 16 || kTile == 32, "tile of 16 or 32 queries");
 #ifndef AHPP_ATTR_PUSH
 #define AHPP_ATTR_PUSH 0          // attribute hop pushed from phase 2 (1) or pulled in phase 1 (0)
 #endif
+#ifndef AHPP_TMA
+#define AHPP_TMA 0                // 1: pull phases gather rows with TMA tile::gather4 (correct, measured 2.6x slower)
+#endif
+#ifndef AHPP_P1_PASSES
+#define AHPP_P1_PASSES 1          // 2: phase 1 gathers the two halves of U in separate passes (measured slower)
+#endif
 #ifndef AHPP_BATCH_MINB
-#define AHPP_BATCH_MINB 3         // resident blocks per SM the register budget targets
+#define AHPP_BATCH_MINB (AHPP_TMA ? 2 : 3)   // resident blocks per SM the register budget targets
 #endif
 
 // Smallest float f with (r > th) <=> (r >= f) for every float r: the mark
@@ -282,7 +289,8 @@ __device__ __forceinline__ Unit unit_of(const ItemList& L, uint32_t u, const uin
 // and clears ta_zero, the buffer the coming phase 2 pushes into.
 template <typename WA>
 __device__ __forceinline__ void gphase1(const BCtx& c, RAcc* A, bool do_v, bool do_a, float* ta_out,
-                                        const float* ta_scan, float* ta_zero, bool count) {
+                                        const float* ta_scan, float* ta_zero, bool count,
+                                        int pass = 0, int npass = 1) {
   const DevGraph& g = c.g;
   const uint32_t lane = c.lane, gl = lane & (kGL - 1), gi = lane / kGL;
   const unsigned gmask = ((1u << kGL) - 1u) << (gi * kGL);
@@ -315,7 +323,13 @@ __device__ __forceinline__ void gphase1(const BCtx& c, RAcc* A, bool do_v, bool 
     Unit un{0, 0, 0, 0xffffffffu};
     const uint32_t* off = is_a ? g.au_off : g.vu_off;
     if (ok) un = is_a ? unit_of(g.b_a, uix - nuv, g.au_off) : unit_of(g.b_v, uix, g.vu_off);
-    const uint32_t b = ok ? off[un.row] + un.b : 0, e = ok ? off[un.row] + un.e : 0;
+    uint32_t b = ok ? off[un.row] + un.b : 0, e = ok ? off[un.row] + un.e : 0;
+    if (ok && npass == 2) {
+      // pass 0 gathers sources u < u_half, pass 1 the rest (entries sorted by u)
+      const uint32_t mid = is_a ? g.au_mid[un.row] : g.vu_mid[un.row];
+      if (pass == 0) e = max(b, min(e, mid));
+      else b = min(e, max(b, mid));
+    }
     const uint32_t stages = warp_max_u32(is_a ? 0u : (e - b + 31) / 32);
     // V rows and attribute rows in one warp: both gathers run, each group
     // keeps the one of its own kind (ranges are empty for the other)
@@ -337,6 +351,15 @@ __device__ __forceinline__ void gphase1(const BCtx& c, RAcc* A, bool do_v, bool 
       s = tot;
     }
     const uint32_t R = un.row;
+    float* out = is_a ? ta_out + (size_t)R * kTile + kQL * gl : c.t.t_v + (size_t)R * kTile + kQL * gl;
+    if (npass == 2 && pass == 0) {             // partial sum of the first half
+      *reinterpret_cast<float4*>(out) = s;
+      continue;
+    }
+    if (npass == 2) {
+      const float4 h = *reinterpret_cast<const float4*>(out);
+      s = make_float4(s.x + h.x, s.y + h.y, s.z + h.z, s.w + h.w);
+    }
     if (!is_a) {
       st_keep4(c.t.t_v + (size_t)R * kTile + kQL * gl, s);
       const uint32_t d = g.vu_off[R + 1] - g.vu_off[R];
@@ -504,6 +527,233 @@ __device__ __forceinline__ void gphase2(const BCtx& c, const LaneCtl* ctl, RAcc*
   flush_q4(part, A);
 }
 
+// ------------------------------------------------------------------------
+// TMA form of the pull phases (one query per lane; kTile == 32).  A warp
+// owns an item (up to 32 consecutive rows, or one chunk of a long row) and
+// walks its neighbour entries in stages of 32 through a two-buffer gather
+// pipeline; row sums go to sp[row][lane] in shared memory.
+#if AHPP_TMA
+static_assert(kTile == 32, "the TMA phases map one query per lane");
+
+template <bool ADD, typename LoadF, typename XF>
+__device__ __forceinline__ void tma_rows(GatherPipe& gp, const CUtensorMap* map, uint32_t nrows,
+                                         uint32_t my_end, uint32_t kb, uint32_t ke, uint32_t lane,
+                                         LoadF load, XF xform, float* sp, unsigned int* err) {
+  if (!ADD)
+    for (uint32_t r = 0; r < nrows; ++r) sp[r * 32 + lane] = 0.f;
+  const uint32_t nst = (ke - kb + kStage - 1) / kStage;
+  uint32_t row = 0;
+  uint32_t row_end = __shfl_sync(kFull, my_end, 0);
+  float acc = 0.f;
+  if (nst == 0) return;
+  uint32_t idx = 0;
+  float coef = 0.f, coef_next = 0.f;
+  {
+    const uint32_t n0 = min((uint32_t)kStage, ke - kb);
+    if (lane < n0) load(kb + lane, idx, coef);
+    pipe_issue(gp, 0, map, lane < n0 ? idx : 0u, n0, lane);
+  }
+  for (uint32_t st = 0; st < nst; ++st) {
+    const int b = st & 1;
+    const uint32_t k0 = kb + st * kStage;
+    const uint32_t n = min((uint32_t)kStage, ke - k0);
+    if (st + 1 < nst) {
+      const uint32_t k1 = k0 + kStage;
+      const uint32_t n1 = min((uint32_t)kStage, ke - k1);
+      uint32_t i1 = 0;
+      coef_next = 0.f;
+      if (lane < n1) load(k1 + lane, i1, coef_next);
+      pipe_issue(gp, b ^ 1, map, lane < n1 ? i1 : 0u, n1, lane);
+    }
+    pipe_wait(gp, b, err);
+    const float* x = gp.buf + b * kStage * 32;
+    for (uint32_t j = 0; j < n; ++j) {
+      const float cj = __shfl_sync(kFull, coef, j);
+      while (k0 + j >= row_end) {
+        sp[row * 32 + lane] += acc;
+        acc = 0.f;
+        ++row;
+        row_end = __shfl_sync(kFull, my_end, row & 31u);
+      }
+      acc = fmaf(cj, xform(x[j * 32 + lane]), acc);
+    }
+    __syncwarp();
+    coef = coef_next;
+  }
+  if (row < nrows) sp[row * 32 + lane] += acc;
+}
+
+// Lane-scalar split-row combine (warp-collective): true for the chunk that
+// finishes the row, with the row total in *tot.
+__device__ __forceinline__ bool split_combine1(const TileBuf& t, uint32_t slot, uint32_t nch, float s,
+                                               uint32_t lane, float* tot) {
+  atomicAdd(&t.split_acc[(size_t)slot * kTile + lane], s);
+  __threadfence();
+  __syncwarp();
+  uint32_t last = 0;
+  if (lane == 0) last = atomicAdd(&t.split_cnt[slot], 1u) == nch - 1;
+  last = __shfl_sync(kFull, last, 0);
+  if (last) {
+    __threadfence();
+    *tot = atomicExch(&t.split_acc[(size_t)slot * kTile + lane], 0.f);
+    if (lane == 0) t.split_cnt[slot] = 0;
+  }
+  return last != 0;
+}
+
+// Item i of a TMA item list: rows [r0, r0 + nrows) whole, or one chunk.
+struct TItem {
+  uint32_t r0, nrows, z, w, slot;   // slot ~0: not split
+  bool chunk;
+};
+__device__ __forceinline__ TItem titem(const ItemList& L, uint32_t i) {
+  const uint4 it = L.items[i];
+  TItem t;
+  t.r0 = it.x;
+  t.chunk = (it.y & (kItemLong | kItemSplit)) != 0;
+  t.nrows = t.chunk ? 1u : it.y;
+  t.z = it.z; t.w = it.w;
+  t.slot = (it.y & kItemSplit) ? (it.y & kItemMask) : 0xffffffffu;
+  return t;
+}
+
+template <typename WA>
+__device__ __forceinline__ void tphase1(const BCtx& c, const TileBuf* tg, GatherPipe& gp, float* sp,
+                                        RAcc* A, unsigned int* err) {
+  const DevGraph& g = c.g;
+  const uint32_t lane = c.lane;
+  Partials part;
+  const uint32_t nv = g.m_v.n_items, total = nv + g.m_a.n_items;
+  auto neg = [](float x) { return fmaxf(-x, 0.f); };
+  for (uint32_t it = c.gw; it < total; it += c.nw) {
+    const bool is_a = it >= nv;
+    const TItem t = titem(is_a ? g.m_a : g.m_v, is_a ? it - nv : it);
+    const uint32_t* off = is_a ? g.au_off : g.vu_off;
+    uint32_t kb, ke, my_end;
+    if (t.chunk) {
+      kb = off[t.r0] + t.z; ke = off[t.r0] + t.w; my_end = ke;
+    } else {
+      kb = off[t.r0];
+      my_end = lane < t.nrows ? off[t.r0 + lane + 1] : 0xffffffffu;
+      ke = __shfl_sync(kFull, my_end, t.nrows - 1);
+    }
+    if (!is_a)
+      tma_rows<false>(gp, &tg->map_ru, t.nrows, my_end, kb, ke, lane,
+                      [&](uint32_t k, uint32_t& i, float& w) { i = ld_stream(g.vu_idx + k); w = ld_stream(g.vu_c + k); },
+                      neg, sp, err);
+    else
+      tma_rows<false>(gp, &tg->map_ru, t.nrows, my_end, kb, ke, lane,
+                      [&](uint32_t k, uint32_t& i, float& w) {
+                        i = ld_stream(g.au_idx + k);
+                        w = wload<WA>(g.au_w, k) * g.rnorm_u[i];
+                      },
+                      neg, sp, err);
+    for (uint32_t row = 0; row < t.nrows; ++row) {
+      const uint32_t R = t.r0 + row;
+      float s = sp[row * 32 + lane];
+      if (t.slot != 0xffffffffu) {
+        const uint32_t slot = t.slot + (is_a ? g.m_v.n_split : 0);
+        const uint32_t nch = is_a ? g.m_a.split_nchunks[t.slot] : g.m_v.split_nchunks[t.slot];
+        float tot;
+        if (!split_combine1(c.t, slot, nch, s, lane, &tot)) continue;
+        s = tot;
+      }
+      if (!is_a) {
+        c.t.t_v[(size_t)R * kTile + lane] = s;
+        if (s > 0.f) part.np_flush += g.vu_off[R + 1] - g.vu_off[R];
+      } else {
+        const float tv = g.k_attr * g.cnorm_a[R] * s;
+        c.t.t_a[(size_t)R * kTile + lane] = tv;
+        if (tv > 0.f) part.np_flush += g.au_off[R + 1] - g.au_off[R];
+      }
+    }
+  }
+  flush_lane_partials(part, A);
+}
+
+// Residue update of row u for this lane's query (see gepilogue2).
+__device__ __forceinline__ void lepilogue2(const BCtx& c, uint32_t u, float s, uint32_t cnt, float th,
+                                           bool act, const LaneCtl* app_ctl, Partials& part) {
+  if (!act) return;
+  const size_t i = (size_t)u * kTile + c.lane;
+  const float r_old = c.t.r_u[i];
+  float kept = r_old;
+  if (r_old < 0.f) {
+    const float add = c.g.alpha * (-r_old);
+    if (c.p.kahan) {
+      float pv = ld_stream(c.t.pi + i), pc = ld_stream(c.t.pic + i);
+      kahan_add(pv, pc, add);
+      __stcs(c.t.pi + i, pv);
+      __stcs(c.t.pic + i, pc);
+    } else {
+      c.t.pi[i] += add;
+    }
+    kept = 0.f;
+  }
+  const float r_new = kept + s;
+  part.max_r = fmaxf(part.max_r, r_new);
+  const bool mark = app_ctl ? (double)r_new > app_ctl[c.lane].eps_f * (double)cnt : r_new >= th;
+  if (mark) {
+    c.t.r_u[i] = -r_new;
+    part.marked += 1;
+    part.marked_deg += cnt;
+  } else {
+    c.t.r_u[i] = r_new;
+  }
+}
+
+template <typename WA>
+__device__ __forceinline__ void tphase2(const BCtx& c, const TileBuf* tg, const LaneCtl* ctl,
+                                        GatherPipe& gp, float* sp, RAcc* A, unsigned int* err) {
+  const DevGraph& g = c.g;
+  const uint32_t lane = c.lane;
+  const bool app = c.p.algo == kAlgoAPP;
+  const LaneCtl& me = ctl[lane];
+  const bool act = me.active != 0;
+  const float th = app ? 0.f : threshold_up(me.phase == kPhaseSync ? 0.0 : me.eps_f);
+  auto id = [](float x) { return x; };
+  auto lv = [&](uint32_t k, uint32_t& i, float& w) { i = ld_stream(g.uv_idx + k); w = ld_stream(g.uv_w + k); };
+  auto la = [&](uint32_t k, uint32_t& i, float& w) { i = ld_stream(g.ua_idx + k); w = wload<WA>(g.ua_w, k); };
+  Partials part;
+  for (uint32_t it = c.gw; it < g.m_u.n_items; it += c.nw) {
+    const TItem t = titem(g.m_u, it);
+    if (t.chunk) {
+      const uint32_t u = t.r0;
+      const uint32_t b1 = g.uv_off[u], dv = g.uv_off[u + 1] - b1;
+      const uint32_t b2 = g.ua_off[u], da = g.ua_off[u + 1] - b2;
+      const uint32_t vb = b1 + min(t.z, dv), ve = b1 + min(t.w, dv);
+      const uint32_t ab = b2 + (t.z > dv ? t.z - dv : 0), ae = b2 + (t.w > dv ? t.w - dv : 0);
+      tma_rows<false>(gp, &tg->map_tv, 1, ve, vb, ve, lane, lv, id, sp, err);
+      tma_rows<true>(gp, &tg->map_ta, 1, ae, ab, ae, lane, la, id, sp, err);
+      float s = sp[lane];
+      if (t.slot != 0xffffffffu) {
+        const uint32_t sl = t.slot + g.m_v.n_split + g.m_a.n_split;
+        float tot;
+        if (!split_combine1(c.t, sl, g.m_u.split_nchunks[t.slot], s, lane, &tot)) continue;
+        s = tot;
+      }
+      lepilogue2(c, u, s, dv + da, th, act, app ? ctl : nullptr, part);
+    } else {
+      const uint32_t r0 = t.r0, nrows = t.nrows;
+      const uint32_t end_v = lane < nrows ? g.uv_off[r0 + lane + 1] : 0xffffffffu;
+      const uint32_t end_a = lane < nrows ? g.ua_off[r0 + lane + 1] : 0xffffffffu;
+      const uint32_t kv0 = g.uv_off[r0], ka0 = g.ua_off[r0];
+      const uint32_t kv1 = __shfl_sync(kFull, end_v, nrows - 1);
+      const uint32_t ka1 = __shfl_sync(kFull, end_a, nrows - 1);
+      tma_rows<false>(gp, &tg->map_tv, nrows, end_v, kv0, kv1, lane, lv, id, sp, err);
+      tma_rows<true>(gp, &tg->map_ta, nrows, end_a, ka0, ka1, lane, la, id, sp, err);
+      const uint32_t beg_v = __shfl_up_sync(kFull, end_v, 1), beg_a = __shfl_up_sync(kFull, end_a, 1);
+      const uint32_t my_cnt = lane < nrows ? (end_v - (lane ? beg_v : kv0)) + (end_a - (lane ? beg_a : ka0)) : 0u;
+      for (uint32_t row = 0; row < nrows; ++row) {
+        const uint32_t cnt = __shfl_sync(kFull, my_cnt, row);
+        lepilogue2(c, r0 + row, sp[row * 32 + lane], cnt, th, act, app ? ctl : nullptr, part);
+      }
+    }
+  }
+  flush_lane_partials(part, A);
+}
+#endif  // AHPP_TMA
+
 __device__ __forceinline__ double bbudget(const BatchParams& p, double eps_f, double M) {
   const double EE = (double)p.e_tot;
   if (p.switch_rule == 2) return INFINITY;
@@ -527,7 +777,7 @@ template <typename WA, bool SERVE>
 __global__ void __launch_bounds__(kThreads, AHPP_BATCH_MINB)
 k_tiles(const __grid_constant__ DevGraph g, const __grid_constant__ BatchState st,
         const __grid_constant__ BatchParams p, const __grid_constant__ ServeParams sv) {
-  extern __shared__ unsigned char smem[];
+  extern __shared__ __align__(1024) unsigned char smem[];
   // Per-query control of the current tile, one entry per lane / query.  Warp 0
   // of every block makes the decisions (all blocks read the same round
   // accumulators after a barrier, so they agree); the phases read it here.
@@ -539,6 +789,25 @@ k_tiles(const __grid_constant__ DevGraph g, const __grid_constant__ BatchState s
   __shared__ uint32_t s_k[kTile];    // top-k size of the lane
   __shared__ int s_flag;
   __shared__ TileBuf s_tb;
+#if AHPP_TMA
+  __shared__ __align__(8) uint64_t s_mbar[kWarps][2];
+  GatherPipe gp;
+  {
+    const uint32_t w = threadIdx.x >> 5;
+    gp.buf = reinterpret_cast<float*>(smem) + (size_t)w * (2 * kStage * 32 + 32 * 32);
+    gp.bar[0] = smem_u32(&s_mbar[w][0]);
+    gp.bar[1] = smem_u32(&s_mbar[w][1]);
+    gp.phase = 0;
+    if ((threadIdx.x & 31) == 0) {
+      mbar_init(gp.bar[0]);
+      mbar_init(gp.bar[1]);
+      mbar_fence_init();
+    }
+    __syncwarp();
+  }
+  float* const sp_tma = reinterpret_cast<float*>(smem) + (size_t)(threadIdx.x >> 5) * (2 * kStage * 32 + 32 * 32) +
+                        2 * kStage * 32;
+#endif
   const uint32_t groups = SERVE ? 1u : p.groups;
   const uint32_t nbg = gridDim.x / groups;              // blocks per group
   const uint32_t grp = blockIdx.x / nbg;
@@ -552,13 +821,15 @@ k_tiles(const __grid_constant__ DevGraph g, const __grid_constant__ BatchState s
   const bool warp0 = threadIdx.x < 32;
   const bool app = p.algo == kAlgoAPP;
   const uint32_t n_work = SERVE ? sv.n_live : (p.n + kTile - 1) / kTile;
-  const uint32_t n_split = g.b_v.n_split + g.b_a.n_split + g.b_u.n_split;
+  const uint32_t n_split = max(g.b_v.n_split + g.b_a.n_split + g.b_u.n_split,
+                               g.m_v.n_split + g.m_a.n_split + g.m_u.n_split);
   const size_t nu32 = (size_t)g.n_u * kTile;
   const uint32_t kmax = p.kmax;
 
   for (uint32_t w = grp; w < n_work; w += groups) {
     const uint32_t tile = SERVE ? sv.live[w] : w;
-    if (threadIdx.x == 0) s_tb = SERVE ? sv.tbufs[tile] : st.tb[grp];
+    const TileBuf* tg = SERVE ? &sv.tbufs[tile] : &st.tb[grp];   // tensor maps live here
+    if (threadIdx.x == 0) s_tb = *tg;
     __syncthreads();
     const uint32_t qi = tile * kTile + lane;            // query (batch) or slot (serve) index
     uint32_t tround = SERVE ? sv.tile_round[tile] : 0u;
@@ -670,14 +941,26 @@ k_tiles(const __grid_constant__ DevGraph g, const __grid_constant__ BatchState s
 
       float* ta_cur = (tround & 1) ? tb.t_a2 : tb.t_a;     // t_A of this round
       float* ta_next = (tround & 1) ? tb.t_a : tb.t_a2;    // t_A of the next round
+#if AHPP_TMA
+      tphase1<WA>(c, tg, gp, sp_tma, A, &tb.bar->err);
+      if (!grid_sync(tb.bar, nbg)) { wait_fail = true; break; }
+      tphase2<WA>(c, tg, s_ctl, gp, sp_tma, A, &tb.bar->err);
+      if (!grid_sync(tb.bar, nbg)) { wait_fail = true; break; }
+      ++tround;
+#else
+      if (AHPP_P1_PASSES == 2) {
+        gphase1<WA>(c, A, true, !AHPP_ATTR_PUSH, ta_cur, nullptr, nullptr, false, 0, 2);
+        if (!grid_sync(tb.bar, nbg)) { wait_fail = true; break; }
+      }
       if (AHPP_ATTR_PUSH)
-        gphase1<WA>(c, A, true, false, nullptr, ta_cur, ta_next, true);
+        gphase1<WA>(c, A, true, false, nullptr, ta_cur, ta_next, true, AHPP_P1_PASSES - 1, AHPP_P1_PASSES);
       else
-        gphase1<WA>(c, A, true, true, ta_cur, nullptr, nullptr, true);
+        gphase1<WA>(c, A, true, true, ta_cur, nullptr, nullptr, true, AHPP_P1_PASSES - 1, AHPP_P1_PASSES);
       if (!grid_sync(tb.bar, nbg)) { wait_fail = true; break; }
       gphase2<WA>(c, s_ctl, A, ta_cur, AHPP_ATTR_PUSH ? ta_next : nullptr);
       if (!grid_sync(tb.bar, nbg)) { wait_fail = true; break; }
       ++tround;
+#endif
 
       if (warp0) {
         LaneCtl L{};
@@ -901,14 +1184,54 @@ template __global__ void k_tiles<__nv_bfloat16, true>(const __grid_constant__ De
                                                       const __grid_constant__ BatchParams,
                                                       const __grid_constant__ ServeParams);
 
-constexpr size_t kBatchSmem = 32 * 1024;   // radix histograms / sort buffer (4096 keys)
+// radix histograms / sort buffer (4096 keys); with TMA also the per-warp
+// gather stages (2 x 32 rows) and row sums (32 rows) of every warp
+constexpr size_t kBatchSmem = AHPP_TMA ? std::max<size_t>(32 * 1024, kWarps * (2 * kStage * 32 + 32 * 32) * 4)
+                                       : 32 * 1024;
 
 namespace {
 const void* tiles_fn(bool bf16, bool serve) {
+  static bool attr_set = false;
+  if (!attr_set) {
+    attr_set = true;
+    const void* fns[4] = {(const void*)k_tiles<__nv_bfloat16, true>, (const void*)k_tiles<float, true>,
+                          (const void*)k_tiles<__nv_bfloat16, false>, (const void*)k_tiles<float, false>};
+    for (const void* f : fns)
+      cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kBatchSmem);
+  }
   if (serve) return bf16 ? (const void*)k_tiles<__nv_bfloat16, true> : (const void*)k_tiles<float, true>;
   return bf16 ? (const void*)k_tiles<__nv_bfloat16, false> : (const void*)k_tiles<float, false>;
 }
 }  // namespace
+
+// Tensor maps of a tile buffer for the TMA row gathers: r_U ([n_u][kTile]),
+// t_V ([n_v][kTile]) and t_A ([n_a][kTile]); box kTile x 1.
+int encode_tile_maps(TileBuf& t, uint32_t n_u, uint32_t n_v, uint32_t n_a) {
+  typedef CUresult (*EncodeFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                               const cuuint64_t*, const cuuint32_t*, const cuuint32_t*,
+                               CUtensorMapInterleave, CUtensorMapSwizzle, CUtensorMapL2promotion,
+                               CUtensorMapFloatOOBfill);
+  static EncodeFn enc = nullptr;
+  if (!enc) {
+    void* fp = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fp, 12000, cudaEnableDefault, &q) !=
+            cudaSuccess || q != cudaDriverEntryPointSuccess || !fp)
+      return -1;
+    enc = (EncodeFn)fp;
+  }
+  auto one = [&](CUtensorMap* m, float* base, uint32_t rows) {
+    const cuuint64_t dims[2] = {(cuuint64_t)kTile, (cuuint64_t)(rows ? rows : 1)};
+    const cuuint64_t strides[1] = {(cuuint64_t)kTile * 4};
+    const cuuint32_t box[2] = {(cuuint32_t)kTile, 1};
+    const cuuint32_t estr[2] = {1, 1};
+    return enc(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, base, dims, strides, box, estr,
+               CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+  };
+  if (!one(&t.map_ru, t.r_u, n_u) || !one(&t.map_tv, t.t_v, n_v) || !one(&t.map_ta, t.t_a, n_a)) return -2;
+  return 0;
+}
 
 int launch_batch(const DevGraph& g, const BatchState& s, const BatchParams& p, bool bf16,
                  int grid, cudaStream_t stream) {

@@ -57,12 +57,19 @@ struct DevGraph {
   const void* au_w = nullptr;
   const float* rnorm_u = nullptr;
   const float* cnorm_a = nullptr;
+  // first entry of each V->U / A->U row whose U id is >= u_half (rows are
+  // sorted by U id): the batched phase 1 gathers the two halves of U in two
+  // passes so that each pass's gather set fits in L2
+  const uint32_t* vu_mid = nullptr;
+  const uint32_t* au_mid = nullptr;
+  uint32_t u_half = 0;
   float alpha = 0.f;
   float k_attr = 0.f;                   // (1 - alpha) * beta
   // single-query (one row per lane / warp-cooperative) work items
   ItemList s1_v, s1_a, s1_u;
-  // batched (one query per lane) work items
+  // batched row-group units, and the TMA items (up to 32 rows per item)
   ItemList b_v, b_a, b_u;
+  ItemList m_v, m_a, m_u;
 };
 
 template <typename WA>
@@ -132,6 +139,9 @@ __device__ __forceinline__ unsigned int ld_acquire_u32(const unsigned int* p) {
 // Barrier over the blocks [0, nblocks) that share `b`.
 __device__ __forceinline__ bool grid_sync(GridBarrier* b, unsigned int nblocks) {
   __shared__ unsigned int s_ok;
+  // data written with ordinary stores before the barrier may be read by TMA
+  // (the async proxy) after it
+  asm volatile("fence.proxy.async.global;" ::: "memory");
   __syncthreads();
   if (threadIdx.x == 0) {
     unsigned int ok = 1;
@@ -155,6 +165,7 @@ __device__ __forceinline__ bool grid_sync(GridBarrier* b, unsigned int nblocks) 
     s_ok = ok;
   }
   __syncthreads();
+  asm volatile("fence.proxy.async.global;" ::: "memory");
   return s_ok != 0;
 }
 

@@ -238,7 +238,8 @@ int ahpp_server_start(ahpp_graph* g, const ahpp_server_opts* opts, ahpp_server**
   if (o.rounds_per_step) s->rounds_per_step = o.rounds_per_step;
   // slots: requested, else what the HBM budget leaves after the graph, else 8 tiles
   const DevGraph& G = g->dg;
-  const size_t n_split = (size_t)G.b_v.n_split + G.b_a.n_split + G.b_u.n_split;
+  const size_t n_split = std::max((size_t)G.b_v.n_split + G.b_a.n_split + G.b_u.n_split,
+                                  (size_t)G.m_v.n_split + G.m_a.n_split + G.m_u.n_split);
   const size_t tile_bytes = (size_t)G.n_u * kTile * 12 + (size_t)std::max(G.n_v, 1u) * kTile * 4 +
                             (size_t)std::max(G.n_a, 1u) * kTile * 4 + std::max<size_t>(n_split, 1) * (kTile + 1) * 4 +
                             (size_t)kRadixPasses * kTile * kRadixBins * 4 + (size_t)kTile * s->kmax * 8 + 4096;
@@ -296,6 +297,7 @@ int ahpp_server_start(ahpp_graph* g, const ahpp_server_opts* opts, ahpp_server**
       b.cand_cnt = (uint32_t*)s->dalloc(kTile * 4);
       ok = b.r_u && b.pi && b.pic && b.t_v && b.t_a && b.t_a2 && b.split_acc && b.split_cnt && b.racc &&
            b.hist && b.cand && b.cand_cnt;
+      if (ok) ok = encode_tile_maps(b, G.n_u, G.n_v, G.n_a) == 0;
       if (ok) {
         // the split accumulators and counters must start at zero (kept zero by the kernel)
         ok = cudaMemset(b.split_acc, 0, std::max<size_t>(n_split, 1) * kTile * 4) == cudaSuccess &&
