@@ -38,7 +38,7 @@ ALPHA, BETA = 0.15, 0.35
 METRIC = "AHPP queries/sec at eps=1e-6 (batched persistent push)"
 
 
-def parse():
+def parse(argv=None):
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=3)
@@ -58,7 +58,7 @@ def parse():
                     help="Poisson arrival rate as a fraction of the measured batched capacity")
     ap.add_argument("--serve-slots", type=int, default=256)
     ap.add_argument("--serve-rounds", type=int, default=4)
-    return ap.parse_args()
+    return ap.parse_args(argv)
 
 
 def graph_spec(name):
@@ -228,6 +228,30 @@ def topk_bytes(info, queries):
     return queries * 4 * info["n_u"]
 
 
+# ------------------------------------------------------------ multi-rank
+
+def max_over_ranks(x, world, device=None):
+    """Largest x over all ranks (the slowest rank sets the job's time)."""
+    if world <= 1:
+        return float(x)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_value(world, batch, steps, t_max):
+    """Queries per second of the whole job: every rank answers `batch`
+    queries per step (weak scaling), all ranks finish within t_max."""
+    return world * batch * steps / t_max
+
+
+def rank_queries(n_u, batch, steps, rank):
+    """Each rank's own query stream, [steps][batch] (replicas share no work)."""
+    return synth.draw_queries(n_u, batch * steps, seed=11 + 1000 * rank).reshape(steps, batch)
+
+
 # ------------------------------------------------------------------ ours
 
 def run_ours(args, rank, world, local_rank):
@@ -248,7 +272,7 @@ def run_ours(args, rank, world, local_rank):
     info = G.info
     stream = torch.cuda.Stream(device=dev)
     B, K, W = args.batch, args.steps, args.warmup
-    qs_all = synth.draw_queries(g.n_u, B * (W + K), seed=11 + 1000 * rank).reshape(W + K, B)
+    qs_all = rank_queries(g.n_u, B, W + K, rank)
     q_t = [torch.from_numpy(qs_all[i].astype(np.int32)).to(dev) for i in range(W + K)]
     eps_t = torch.full((B,), args.eps, dtype=torch.float64, device=dev)
     k_t = torch.full((B,), args.k, dtype=torch.int32, device=dev)
@@ -295,13 +319,8 @@ def run_ours(args, rank, world, local_rank):
     tile = int(info["batch_tile"])
     tile_rounds = int(sum(rounds[i:i + tile].max() for i in range(0, B, tile)))
 
-    # max over ranks
-    t_max = dev_s
-    if world > 1:
-        t = torch.tensor([dev_s], dtype=torch.float64, device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        t_max = float(t.item())
-    value = world * B * K / t_max
+    t_max = max_over_ranks(dev_s, world, dev)
+    value = whole_job_value(world, B, K, t_max)
 
     # e2e through the host API (pinned-free host numpy buffers, copies inside)
     e2e = None
@@ -312,12 +331,8 @@ def run_ours(args, rank, world, local_rank):
         te = time.perf_counter()
         for j in range(K):
             G.query_batch(host_q[j], args.eps, args.k)
-        te = time.perf_counter() - te
-        if world > 1:
-            t = torch.tensor([te], dtype=torch.float64, device=dev)
-            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-            te = float(t.item())
-        e2e = {"value": world * B * K / te, "unit": "queries/s",
+        te = max_over_ranks(time.perf_counter() - te, world, dev)
+        e2e = {"value": whole_job_value(world, B, K, te), "unit": "queries/s",
                "h2d_bytes_per_step": B * (4 + 8 + 4),
                "d2h_bytes_per_step": B * (args.k * 8 + 4 + ahpp.STATS_BYTES)}
 

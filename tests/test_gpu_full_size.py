@@ -1,0 +1,107 @@
+"""Parity at the full workload sizes, in the launch configuration bench.py times.
+
+Medium (|U|=1M, |V|=500k, |E|=20M, |A|=10k x 20, bf16 attribute weights):
+one query is compared element by element with the FP64 oracle push (the
+oracle takes about half a minute), and the same query inside a 64-query
+batched launch (two tiles, bench's kernel and grid) is compared with both.
+Every query of the batch is checked for properties that hold at any size.
+
+Large (|U|=|V|=5M, |E|=200M, |A|=50k x 30): too big for the oracle's exact
+push in a test, so it is checked through properties that hold at any size:
+mass conservation, nonnegativity, the batched result equal to the result
+alone, and top-k consistent with the reserves.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2512_11606_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+ALPHA, BETA = 0.15, 0.35
+TOL = 1e-6
+
+
+@pytest.fixture(scope="module")
+def ahpp():
+    from paper_2512_11606_gb300 import build
+    build.build()
+    from paper_2512_11606_gb300 import ahpp as mod
+    return mod
+
+
+@pytest.fixture(scope="module")
+def medium(ahpp):
+    g = synth.make_graph(**synth.MEDIUM_BF16)
+    og = oracle.OracleGraph.from_arrays(g)
+    lam, _ = og.lambda_estimate(ALPHA, BETA)
+    G = ahpp.Graph.from_arrays(g, lam=lam)
+    yield dict(g=g, og=og, lam=lam, G=G)
+    G.close()
+
+
+def test_medium_lambda_on_gpu_matches_oracle(ahpp, medium):
+    G2 = ahpp.Graph.from_arrays(medium["g"])
+    lam_gpu = G2.lam
+    G2.close()
+    assert lam_gpu >= medium["lam"] * (1 - 1e-6)
+    assert abs(lam_gpu - medium["lam"]) / medium["lam"] <= 2e-4
+
+
+def test_medium_single_and_batched_vs_oracle(medium):
+    G, og, lam, g = medium["G"], medium["og"], medium["lam"], medium["g"]
+    q1024 = [int(x) for x in synth.draw_queries(g.n_u, 1024)]
+    qs = q1024[:64]
+    q = qs[0]
+    eps = 1e-6
+    ref = og.push("asrp", ALPHA, BETA, q, eps, lam=lam)
+    alone, st, rc = G.query_dense(q, eps)
+    assert rc == 0
+    assert np.abs(alone.astype(np.float64) - ref.pi).max() <= TOL
+    assert abs(st["rounds"] - ref.stats["rounds"]) <= 1
+    dense, stats, rc = G.query_batch_dense(qs, eps)
+    assert rc == 0
+    assert np.abs(dense[0].astype(np.float64) - ref.pi).max() <= TOL
+    assert np.abs(dense[0] - alone).max() <= TOL
+    for i in range(len(qs)):
+        s = stats[i]
+        assert s["status"] == 0 and s["mass_err"] < 1e-5
+        assert dense[i].min() >= 0.0 and dense[i][qs[i]] >= ALPHA - TOL
+        assert s["max_resid"] <= eps / lam * (1 + 1e-6)
+
+    # the launch bench.py times: 1,024 queries, top-100 each
+    k = 100
+    res = G.query_batch(q1024, eps, k)
+    assert all(r.rc == 0 and r.stats["status"] == 0 for r in res)
+    top = res[0]
+    assert top.nodes.shape[0] == k
+    assert np.all(np.diff(top.scores) <= 0)
+    assert np.abs(top.scores.astype(np.float64) - ref.pi[top.nodes]).max() <= TOL
+    kth = np.sort(ref.pi)[-k]
+    assert ref.pi[top.nodes].min() >= kth - 2 * TOL      # a valid top-k of the oracle's scores
+    for i in range(1, 64):
+        r = res[i]
+        assert np.abs(r.scores - dense[i][r.nodes]).max() <= TOL
+        kth_i = np.sort(dense[i])[-k]
+        assert dense[i][r.nodes].min() >= kth_i - 2 * TOL
+
+
+@pytest.mark.slow
+def test_large_graph_properties(ahpp):
+    g = synth.make_graph(**synth.LARGE)
+    G = ahpp.Graph.from_arrays(g)
+    try:
+        info = G.info
+        assert info["n_e"] == g.n_e and info["n_ea"] == g.n_ea
+        qs = [int(x) for x in synth.draw_queries(g.n_u, 32)]
+        eps = 1e-6
+        alone, st, rc = G.query_dense(qs[0], eps)
+        assert rc == 0 and st["mass_err"] < 1e-5 and alone.min() >= 0.0
+        res = G.query_batch(qs, eps, 1000)
+        assert all(r.rc == 0 and r.stats["mass_err"] < 1e-5 for r in res)
+        top = res[0]
+        assert top.nodes.shape[0] == 1000
+        np.testing.assert_allclose(top.scores, alone[top.nodes], rtol=1e-5, atol=TOL)
+        assert res[0].stats["rounds"] == st["rounds"]
+    finally:
+        G.close()
