@@ -6,11 +6,15 @@ oracle takes about half a minute), and the same query inside a 64-query
 batched launch (two tiles, bench's kernel and grid) is compared with both.
 Every query of the batch is checked for properties that hold at any size.
 
-Large (|U|=|V|=5M, |E|=200M, |A|=50k x 30): too big for the oracle's exact
-push in a test, so it is checked through properties that hold at any size:
-mass conservation, nonnegativity, the batched result equal to the result
-alone, and top-k consistent with the reserves.
+Large (|U|=|V|=5M, |E|=200M, |A|=50k x 30, 256-query batch, top-1,000):
+too big for the oracle's exact push in a test, so it is checked through
+properties that hold at any size: mass conservation, nonnegativity, the
+batched result equal to the result alone, and top-k consistent with the
+reserves.  Generating that graph takes minutes on the host, so the test runs
+only with AHPP_LARGE=1.
 """
+import os
+
 import numpy as np
 import pytest
 
@@ -67,7 +71,8 @@ def test_medium_single_and_batched_vs_oracle(medium):
         s = stats[i]
         assert s["status"] == 0 and s["mass_err"] < 1e-5
         assert dense[i].min() >= 0.0 and dense[i][qs[i]] >= ALPHA - TOL
-        assert s["max_resid"] <= eps / lam * (1 + 1e-6)
+        assert s["max_resid"] <= s["eps_f"] * (1 + 1e-6)
+        assert s["eps_f"] <= eps / lam * (1 + 1e-6)
 
     # the launch bench.py times: 1,024 queries, top-100 each
     k = 100
@@ -87,21 +92,24 @@ def test_medium_single_and_batched_vs_oracle(medium):
 
 
 @pytest.mark.slow
+@pytest.mark.skipif(os.environ.get("AHPP_LARGE") != "1",
+                    reason="large graph: about 3 minutes of host-side generation; set AHPP_LARGE=1")
 def test_large_graph_properties(ahpp):
     g = synth.make_graph(**synth.LARGE)
     G = ahpp.Graph.from_arrays(g)
     try:
         info = G.info
         assert info["n_e"] == g.n_e and info["n_ea"] == g.n_ea
-        qs = [int(x) for x in synth.draw_queries(g.n_u, 32)]
+        qs = [int(x) for x in synth.draw_queries(g.n_u, 256)]
         eps = 1e-6
         alone, st, rc = G.query_dense(qs[0], eps)
         assert rc == 0 and st["mass_err"] < 1e-5 and alone.min() >= 0.0
-        res = G.query_batch(qs, eps, 1000)
+        assert alone[qs[0]] >= ALPHA - TOL
+        res = G.query_batch(qs, eps, 1000)       # 256-query batch, top-1,000
         assert all(r.rc == 0 and r.stats["mass_err"] < 1e-5 for r in res)
         top = res[0]
         assert top.nodes.shape[0] == 1000
         np.testing.assert_allclose(top.scores, alone[top.nodes], rtol=1e-5, atol=TOL)
-        assert res[0].stats["rounds"] == st["rounds"]
+        assert abs(res[0].stats["rounds"] - st["rounds"]) <= 1
     finally:
         G.close()
