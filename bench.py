@@ -56,7 +56,7 @@ def parse(argv=None):
                     help="open-loop serving window (0 disables the serving measurement)")
     ap.add_argument("--serve-load", type=float, default=0.8,
                     help="Poisson arrival rate as a fraction of the measured batched capacity")
-    ap.add_argument("--serve-slots", type=int, default=256)
+    ap.add_argument("--serve-slots", type=int, default=64)
     ap.add_argument("--serve-rounds", type=int, default=4)
     return ap.parse_args(argv)
 
@@ -228,6 +228,32 @@ def topk_bytes(info, queries):
     return queries * 4 * info["n_u"]
 
 
+# DRAM bytes (read + write) per tile-round of k_tiles on the medium graph, from
+# the ncu capture summarised in profiles/k_tiles_medium_tile32.md (373.61 GB over
+# the 106 rounds of one 32-query tile).  It describes the kernel built from the
+# sources listed by hash; once any of them changes the figure no longer applies.
+NCU_TRAFFIC = {
+    "graph": "medium",
+    "bytes_per_tile_round": 373.61e9 / 106,
+    "sources": {"ahpp_batch.cu": "5fc4c43e20957b74", "ahpp_batch.cuh": "f3dfbbd4287bd668",
+                "ahpp_internal.cuh": "5d60c05c7f5e231d"},
+}
+
+
+def ncu_traffic(graph, tile_rounds):
+    """DRAM bytes of one launch scaled from the capture, or None if it does
+    not describe the kernel as built now."""
+    import hashlib
+    if graph != NCU_TRAFFIC["graph"]:
+        return None
+    csrc = os.path.join(ROOT, "paper_2512_11606_gb300", "csrc")
+    for name, want in NCU_TRAFFIC["sources"].items():
+        with open(os.path.join(csrc, name), "rb") as f:
+            if hashlib.sha256(f.read()).hexdigest()[:16] != want:
+                return None
+    return NCU_TRAFFIC["bytes_per_tile_round"] * tile_rounds
+
+
 # ------------------------------------------------------------ multi-rank
 
 def max_over_ranks(x, world, device=None):
@@ -369,9 +395,11 @@ def run_ours(args, rank, world, local_rank):
     alg = tile_rounds * round_bytes(info, tile) + topk_bytes(info, B)   # one launch (last step)
     achieved = alg / (sum(launch_ms) / K / 1e3) / 1e9
     roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-            "frac": achieved / peak, "traffic": None,
+            "frac": achieved / peak, "traffic": ncu_traffic(args.graph, tile_rounds),
+            "traffic_note": ("ncu dram__bytes_read.sum + dram__bytes_write.sum of one 32-query tile "
+                             "(106 rounds), scaled by the launch's tile-rounds"),
             "peak_source": f"{peak_kind} hbm_gbs (MEASURED_PEAKS.json)",
-            "kernel": "k_batch (persistent, all rounds + top-k of one 1,024-query step)",
+            "kernel": "k_tiles (persistent: all rounds + top-k of one 1,024-query step)",
             "algorithmic_bytes_per_launch": alg,
             "tile_rounds_per_launch": tile_rounds}
 
@@ -414,16 +442,51 @@ def run_ours(args, rank, world, local_rank):
 
 
 def run_serving(ahpp, G, g, args, rate):
-    """Submit an open-loop Poisson stream at `rate` queries/s for
-    args.serve_seconds; report completed queries/s and submit-to-result
-    latency percentiles (measured by the server)."""
-    n = max(32, int(rate * args.serve_seconds))
-    t_arr, q, _, _ = synth.draw_stream(n, rate, g.n_u, seed=101)
+    """Continuous batching through the server API, two measurements.
+
+    saturated: closed loop with as many requests in flight as slots (a new
+    request is submitted as each result is taken); completed queries/s and
+    submit-to-result latency over a steady-state window (ramp-up and drain
+    excluded).
+    open_loop: Poisson arrivals at `rate` queries/s for args.serve_seconds;
+    completed queries/s and latency percentiles of every request.
+    """
+    out = {"slots": None, "rounds_per_step": args.serve_rounds}
     srv = ahpp.Server(G, max_slots=args.serve_slots, rounds_per_step=args.serve_rounds)
     try:
-        warm = [srv.submit(int(x), args.eps, args.k) for x in q[:8]]
+        slots = srv.info()["slots"]
+        out["slots"] = slots
+        warm = [srv.submit(int(x), args.eps, args.k) for x in synth.draw_queries(g.n_u, 8, seed=99)]
         for t in warm:
             srv.wait(t, args.k)
+
+        # saturated (closed loop)
+        n_sat = max(4 * slots, int(args.serve_seconds * rate / max(args.serve_load, 1e-3) / 2))
+        qs = synth.draw_queries(g.n_u, n_sat, seed=202)
+        pending = [srv.submit(int(q), args.eps, args.k) for q in qs[:slots]]
+        nxt = slots
+        done_t, lat = [], []
+        t0 = time.perf_counter()
+        while pending:
+            r = srv.wait(pending.pop(0), args.k)
+            done_t.append(time.perf_counter() - t0)
+            lat.append(r.stats["served_ms"])
+            if nxt < n_sat:
+                pending.append(srv.submit(int(qs[nxt]), args.eps, args.k))
+                nxt += 1
+        lo, hi = slots, n_sat - slots          # steady state: after the first wave, before the drain
+        if hi - lo >= 8:
+            out["saturated"] = {
+                "qps": (hi - lo) / (done_t[hi - 1] - done_t[lo - 1]),
+                "p50_ms": statistics.median(lat[lo:hi]),
+                "p99_ms": float(np.percentile(lat[lo:hi], 99)),
+                "queries": n_sat, "window_queries": hi - lo,
+                "note": "closed loop, requests in flight = slots; qps over the steady-state window",
+            }
+
+        # open loop (Poisson arrivals)
+        n = max(32, int(rate * args.serve_seconds))
+        t_arr, q, _, _ = synth.draw_stream(n, rate, g.n_u, seed=101)
         tickets = []
         t0 = time.perf_counter()
         for i in range(n):
@@ -433,16 +496,21 @@ def run_serving(ahpp, G, g, args, rate):
             tickets.append(srv.submit(int(q[i]), args.eps, args.k))
         lat = []
         for t in tickets:
-            r = srv.wait(t, args.k)
-            lat.append(r.stats["served_ms"])
+            lat.append(srv.wait(t, args.k).stats["served_ms"])
         span = time.perf_counter() - t0
-        info = srv.info()
+        out["open_loop"] = {
+            "rate_qps": rate, "queries": n, "qps": n / span, "p50_ms": statistics.median(lat),
+            "p99_ms": float(np.percentile(lat, 99)),
+            "note": "Poisson arrivals at rate_qps; qps = completed / (last result - first submit)",
+        }
+        out["steps"] = srv.info()["steps"]
     finally:
         srv.stop()
-    return {"rate_qps": rate, "queries": n, "qps": n / span, "p50_ms": statistics.median(lat),
-            "p99_ms": float(np.percentile(lat, 99)), "slots": info["slots"],
-            "rounds_per_step": args.serve_rounds, "steps": info["steps"],
-            "note": "open-loop Poisson arrivals at the given rate; qps = completed / (last result - first submit)"}
+    sat = out.get("saturated")
+    out["qps"] = sat["qps"] if sat else out["open_loop"]["qps"]
+    out["p50_ms"] = sat["p50_ms"] if sat else out["open_loop"]["p50_ms"]
+    out["p99_ms"] = sat["p99_ms"] if sat else out["open_loop"]["p99_ms"]
+    return out
 
 
 def run_reference(args, rank, world):
