@@ -65,18 +65,16 @@ __device__ __forceinline__ void flush_lane_partials(Partials& p, RAcc* acc) {
 // tile's 32 queries (lane l of the group: queries 4l .. 4l+3).  One gather
 // is a float4 load per lane, so the group reads the 32 queries' values of a
 // neighbour as one 128-byte line and one warp instruction moves 4 lines.
-// Entries are staged 32 at a time (4 per lane, coalesced), then gathered 8
-// at a time with all 8 loads in flight before they are consumed.
+// Entries go in waves of 8 (one per lane of the group, coalesced): the 8
+// line gathers of a wave are in flight together, and the number of waves is
+// the warp's longest row, so short rows (most rows of a power-law graph)
+// issue no idle gather slots beyond their last wave.
 constexpr int kQL = 4;                 // queries per lane
 constexpr int kGL = kTile / kQL;       // lanes per row group (one 128- or 64-byte line)
 constexpr int kGPW = 32 / kGL;         // row groups per warp
-constexpr int kSlots = 32 / kGL;       // staged entries per lane per 32-entry stage
 static_assert(kTile == 16 || kTile == 32, "tile of 16 or 32 queries");
-#ifndef AHPP_BATCH_WAVES
-#define AHPP_BATCH_WAVES 1        // 8-entry gather waves issued together (1 or 2)
-#endif
 #ifndef AHPP_ATTR_PUSH
-#define AHPP_ATTR_PUSH 0          // attribute hop pushed from phase 2 (1) or pulled in phase 1 (0)
+#define AHPP_ATTR_PUSH 1          // attribute hop pushed from phase 2 (1) or pulled in phase 1 (0); 1 measured faster
 #endif
 #ifndef AHPP_TMA
 #define AHPP_TMA 0                // 1: pull phases gather rows with TMA tile::gather4 (correct, measured 2.6x slower)
@@ -85,7 +83,7 @@ static_assert(kTile == 16 || kTile == 32, "tile of 16 or 32 queries");
 #define AHPP_P1_PASSES 1          // 2: phase 1 gathers the two halves of U in separate passes (measured slower)
 #endif
 #ifndef AHPP_BATCH_MINB
-#define AHPP_BATCH_MINB (AHPP_TMA ? 2 : 3)   // resident blocks per SM the register budget targets
+#define AHPP_BATCH_MINB (AHPP_TMA ? 2 : (AHPP_ATTR_PUSH ? 3 : 4))   // resident blocks per SM the register budget targets (measured best)
 #endif
 
 // Smallest float f with (r > th) <=> (r >= f) for every float r: the mark
@@ -145,43 +143,46 @@ __device__ __forceinline__ float4 f4_fma(float c, float4 x, float4 a) {
   return make_float4(fmaf(c, x.x, a.x), fmaf(c, x.y, a.y), fmaf(c, x.z, a.z), fmaf(c, x.w, a.w));
 }
 
-// Sum over the entries [b, e) of this group's row of coef(k) * gather(idx(k)).
-// Called by the whole warp (control is warp-uniform; rounds = the warp's
-// maximum number of 32-entry stages); a group with b == e adds nothing.
+// Sum over the entries [b, e) of this group's row of coef(k) * gather(idx(k)),
+// in waves of kGL entries: lane t of the group loads entry t of a wave
+// (coalesced), the entry's index and coefficient are broadcast within the
+// group, and the wave's kGL row gathers are in flight together.  The next
+// wave's index and coefficient loads are issued before the current wave's
+// gathers.  Called by the whole warp: `waves` is warp-uniform (the warp's
+// longest range, in waves); a group with b == e adds nothing.
 template <typename LoadF, typename GatherF>
-__device__ __forceinline__ float4 group_accum(uint32_t b, uint32_t e, uint32_t stages, uint32_t gl,
+__device__ __forceinline__ float4 group_accum(uint32_t b, uint32_t e, uint32_t waves, uint32_t gl,
                                               LoadF load, GatherF gather) {
-  float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
-  for (uint32_t st = 0; st < stages; ++st) {
-    const uint32_t k0 = b + st * 32;
-    const uint32_t n = k0 < e ? min(32u, e - k0) : 0u;
-    uint32_t mi[kSlots];
-    float mc[kSlots];
+  float2 a01 = make_float2(0.f, 0.f), a23 = make_float2(0.f, 0.f);
+  uint32_t k = b + gl;
+  uint32_t mi = 0;
+  float mc = 0.f;
+  if (k < e) load(k, mi, mc);
+  for (uint32_t w = 0; w < waves; ++w) {
+    const uint32_t k0 = b + w * kGL;
+    const uint32_t n = k0 < e ? min((uint32_t)kGL, e - k0) : 0u;
+    const uint32_t kn = k + kGL;
+    uint32_t ni = 0;
+    float nc = 0.f;
+    if (kn < e) load(kn, ni, nc);
+    float4 x[kGL];
 #pragma unroll
-    for (int s = 0; s < kSlots; ++s) {
-      const uint32_t j = gl + kGL * s;
-      mi[s] = 0; mc[s] = 0.f;
-      if (j < n) load(k0 + j, mi[s], mc[s]);
+    for (int t = 0; t < kGL; ++t) {
+      const uint32_t id = __shfl_sync(kFull, mi, t, kGL);
+      x[t] = (uint32_t)t < n ? gather(id) : make_float4(0.f, 0.f, 0.f, 0.f);
     }
-    constexpr int W = AHPP_BATCH_WAVES;
 #pragma unroll
-    for (int s = 0; s < kSlots; s += W) {
-      float4 x[W * kGL];
-#pragma unroll
-      for (int h = 0; h < W; ++h)
-#pragma unroll
-        for (int t = 0; t < kGL; ++t) {
-          const uint32_t id = __shfl_sync(kFull, mi[s + h], t, kGL);
-          x[h * kGL + t] = (uint32_t)(kGL * (s + h) + t) < n ? gather(id) : make_float4(0.f, 0.f, 0.f, 0.f);
-        }
-#pragma unroll
-      for (int h = 0; h < W; ++h)
-#pragma unroll
-        for (int t = 0; t < kGL; ++t)
-          acc = f4_fma(__shfl_sync(kFull, mc[s + h], t, kGL), x[h * kGL + t], acc);
+    for (int t = 0; t < kGL; ++t) {
+      const float c = __shfl_sync(kFull, mc, t, kGL);
+      const float2 cc = make_float2(c, c);
+      a01 = __ffma2_rn(cc, make_float2(x[t].x, x[t].y), a01);
+      a23 = __ffma2_rn(cc, make_float2(x[t].z, x[t].w), a23);
     }
+    mi = ni;
+    mc = nc;
+    k = kn;
   }
-  return acc;
+  return make_float4(a01.x, a01.y, a23.x, a23.y);
 }
 
 __device__ __forceinline__ uint32_t warp_max_u32(uint32_t v) {
@@ -330,17 +331,14 @@ __device__ __forceinline__ void gphase1(const BCtx& c, RAcc* A, bool do_v, bool 
       if (pass == 0) e = max(b, min(e, mid));
       else b = min(e, max(b, mid));
     }
-    const uint32_t stages = warp_max_u32(is_a ? 0u : (e - b + 31) / 32);
+    const uint32_t waves = warp_max_u32(is_a ? 0u : (e - b + kGL - 1) / kGL);
     // V rows and attribute rows in one warp: both gathers run, each group
     // keeps the one of its own kind (ranges are empty for the other)
-    const float4 sv = group_accum(is_a ? 0u : b, is_a ? 0u : e, stages, gl,
+    const float4 sv = group_accum(is_a ? 0u : b, is_a ? 0u : e, waves, gl,
         [&](uint32_t k, uint32_t& i, float& w) { i = ld_stream(g.vu_idx + k); w = ld_stream(g.vu_c + k); }, gp);
-    const uint32_t stages_a = warp_max_u32(is_a ? (e - b + 31) / 32 : 0u);
-    const float4 sa = group_accum(is_a ? b : 0u, is_a ? e : 0u, stages_a, gl,
-        [&](uint32_t k, uint32_t& i, float& w) {
-          i = ld_stream(g.au_idx + k);
-          w = wload<WA>(g.au_w, k) * g.rnorm_u[i];
-        }, gp);
+    const uint32_t waves_a = warp_max_u32(is_a ? (e - b + kGL - 1) / kGL : 0u);
+    const float4 sa = group_accum(is_a ? b : 0u, is_a ? e : 0u, waves_a, gl,
+        [&](uint32_t k, uint32_t& i, float& w) { i = ld_stream(g.au_idx + k); w = ld_stream(g.au_c + k); }, gp);
     if (!ok) continue;
     float4 s = is_a ? sa : sv;
     if (un.slot != 0xffffffffu) {
@@ -437,31 +435,23 @@ __device__ __forceinline__ void push_attr(const DevGraph& g, uint32_t u, float4 
   if (!__any_sync(gmask, mine)) return;               // group-uniform
   const uint32_t b = g.ua_off[u], e = g.ua_off[u + 1];
   const float f = g.k_attr * g.rnorm_u[u];
-  for (uint32_t k0 = b; k0 < e; k0 += kGL * kSlots) {
-    // stage up to 32 entries over the group's lanes (coalesced), then every
-    // lane issues one float4 atomic per entry for its 4 queries
-    const uint32_t n = min((uint32_t)(kGL * kSlots), e - k0);
-    uint32_t mi[kSlots];
-    float mc[kSlots];
-#pragma unroll
-    for (int s = 0; s < kSlots; ++s) {
-      const uint32_t j = gl + kGL * s;
-      mi[s] = 0; mc[s] = 0.f;
-      if (j < n) {
-        mi[s] = g.ua_idx[k0 + j];
-        mc[s] = f * wload<WA>(g.ua_w, k0 + j) * g.cnorm_a[mi[s]];
-      }
+  // waves of kGL entries (one per lane of the group, coalesced); every lane
+  // then issues one float4 reduction per entry for its 4 queries
+  for (uint32_t k0 = b; k0 < e; k0 += kGL) {
+    const uint32_t n = min((uint32_t)kGL, e - k0);
+    uint32_t mi = 0;
+    float mc = 0.f;
+    if (gl < n) {
+      mi = g.ua_idx[k0 + gl];
+      mc = f * wload<WA>(g.ua_w, k0 + gl) * g.cnorm_a[mi];
     }
 #pragma unroll
-    for (int s = 0; s < kSlots; ++s) {
-#pragma unroll
-      for (int t = 0; t < kGL; ++t) {
-        const uint32_t a = __shfl_sync(gmask, mi[s], t, kGL);
-        const float cf = __shfl_sync(gmask, mc[s], t, kGL);
-        if ((uint32_t)(kGL * s + t) < n && mine)
-          atomicAdd(reinterpret_cast<float4*>(ta_push + (size_t)a * kTile + kQL * gl),
-                    make_float4(cf * p.x, cf * p.y, cf * p.z, cf * p.w));
-      }
+    for (int t = 0; t < kGL; ++t) {
+      const uint32_t a = __shfl_sync(gmask, mi, t, kGL);
+      const float cf = __shfl_sync(gmask, mc, t, kGL);
+      if ((uint32_t)t < n && mine)
+        atomicAdd(reinterpret_cast<float4*>(ta_push + (size_t)a * kTile + kQL * gl),
+                  make_float4(cf * p.x, cf * p.y, cf * p.z, cf * p.w));
     }
   }
 }
@@ -508,7 +498,7 @@ __device__ __forceinline__ void gphase2(const BCtx& c, const LaneCtl* ctl, RAcc*
     // chunk [z, w) of the combined list: V neighbours first, then attributes
     const uint32_t vb = b1 + min(z, dv), ve = b1 + min(w, dv);
     const uint32_t ab = b2 + (z > dv ? z - dv : 0), ae = b2 + (w > dv ? w - dv : 0);
-    const uint32_t sv = warp_max_u32((ve - vb + 31) / 32), sa = warp_max_u32((ae - ab + 31) / 32);
+    const uint32_t sv = warp_max_u32((ve - vb + kGL - 1) / kGL), sa = warp_max_u32((ae - ab + kGL - 1) / kGL);
     float4 s = group_accum(vb, ve, sv, gl,
         [&](uint32_t k, uint32_t& i, float& wt) { i = ld_stream(g.uv_idx + k); wt = ld_stream(g.uv_w + k); }, gv);
     const float4 s2 = group_accum(ab, ae, sa, gl,
@@ -645,7 +635,7 @@ __device__ __forceinline__ void tphase1(const BCtx& c, const TileBuf* tg, Gather
       tma_rows<false>(gp, &tg->map_ru, t.nrows, my_end, kb, ke, lane,
                       [&](uint32_t k, uint32_t& i, float& w) {
                         i = ld_stream(g.au_idx + k);
-                        w = wload<WA>(g.au_w, k) * g.rnorm_u[i];
+                        w = g.au_c[k];
                       },
                       neg, sp, err);
     for (uint32_t row = 0; row < t.nrows; ++row) {

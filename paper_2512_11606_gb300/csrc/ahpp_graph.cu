@@ -296,6 +296,16 @@ int build_graph(const ahpp_graph_desc* d, ahpp_graph* g) {
   std::vector<float> rnorm(nU), cnorm(nA);
   for (uint32_t u = 0; u < nU; ++u) rnorm[u] = wr[u] > 0 ? (float)(1.0 / wr[u]) : 0.f;
   for (uint32_t a = 0; a < nA; ++a) cnorm[a] = wc[a] > 0 ? (float)(1.0 / wc[a]) : 0.f;
+  // pull coefficient of the A->U direction (the U-side factor of Eq. 2), from
+  // the quantised weight and the FP64 row sum, rounded once to FP32
+  std::vector<float> f_au_c(au_w.size());
+  parallel_for(nA, [&](size_t b, size_t e) {
+    for (size_t a = b; a < e; ++a)
+      for (uint32_t k = au_off[a]; k < au_off[a + 1]; ++k) {
+        const uint32_t u = au_idx[k];
+        f_au_c[k] = wr[u] > 0 ? (float)(au_w[k] / wr[u]) : 0.f;
+      }
+  });
 
   // 5. work items (rows are sorted by degree, longest first)
   std::vector<uint32_t> dg_u(nU), dg_v(nV), dg_a(nA);
@@ -357,6 +367,7 @@ int build_graph(const ahpp_graph_desc* d, ahpp_graph* g) {
     G.vu_mid = (const uint32_t*)up(vmid.data(), vmid.size() * 4);
     G.au_mid = (const uint32_t*)up(amid.data(), amid.size() * 4);
   }
+  G.au_c = (const float*)up(f_au_c.data(), f_au_c.size() * 4);
   G.rnorm_u = (const float*)up(rnorm.data(), rnorm.size() * 4);
   G.cnorm_a = (const float*)up(cnorm.data(), cnorm.size() * 4);
   auto up_items = [&](const HostItems& h, ItemList& L) {

@@ -84,7 +84,7 @@ __device__ void phase1(const Ctx& c, Partials& part) {
       } else {
         for (uint32_t k = item.z + lane; k < item.w; k += 32) {
           uint32_t u = idx[base + k];
-          s = fmaf(wload<WA>(g.au_w, base + k) * g.rnorm_u[u], pushed(c.s.r_u, u), s);
+          s = fmaf(g.au_c[base + k], pushed(c.s.r_u, u), s);
         }
       }
       s = warp_sum(s);
@@ -113,7 +113,7 @@ __device__ void phase1(const Ctx& c, Partials& part) {
       } else {
         for (uint32_t k = b; k < e; ++k) {
           uint32_t u = idx[k];
-          s = fmaf(wload<WA>(g.au_w, k) * g.rnorm_u[u], pushed(c.s.r_u, u), s);
+          s = fmaf(g.au_c[k], pushed(c.s.r_u, u), s);
         }
       }
       p1_epilogue(c, is_a, row, s, part);
