@@ -210,17 +210,19 @@ def measured_peak():
 def round_bytes(info, lanes, bf16=True):
     """Algorithmic DRAM bytes of one pull round of a tile with `lanes` queries.
 
-    Graph (once per round, shared by the lanes): phase 1 streams V->U
-    (index + coefficient, 8 B/edge) and A->U (index + weight, 6 B with bf16);
-    phase 2 streams U->V (8 B/edge) and U->A (6 B); row offsets of the four
-    directions.  State (per lane): phase 1 reads r_U once and writes t_V and
-    t_A; phase 2 reads t_V and t_A once, reads and writes r_U, and
-    read-modify-writes the reserve and its Kahan compensation.
+    Graph (once per round, shared by the lanes): phase 1 streams V->U (index
+    + coefficient, 8 B/edge); phase 2 streams U->V (index + weight, 8 B/edge)
+    and U->A once (index + bf16 weight, 6 B/entry; the attribute push reuses
+    the entries the gather read); row offsets of the three directions and the
+    U-side attribute normaliser.  State (per lane): phase 1 reads r_U once,
+    writes t_V, scans t_A and clears the next t_A; phase 2 reads t_V and t_A
+    once, reads and writes r_U, and read-modify-writes the reserve and its
+    Kahan compensation.
     """
     wa = 2 if bf16 else 4
     nU, nV, nA, nE, nEA = (info[k] for k in ("n_u", "n_v", "n_a", "n_e", "n_ea"))
-    graph = 2 * (4 + 4) * nE + 2 * (4 + wa) * nEA + 4 * (2 * nU + nV + nA + 4) + 4 * nU
-    state = lanes * 4 * (nU + nV + nA + nV + nA + 2 * nU + 4 * nU)
+    graph = 2 * (4 + 4) * nE + (4 + wa) * nEA + 4 * (2 * (nU + 1) + nV + 1) + 4 * nU + 4 * nA
+    state = lanes * 4 * (nU + nV + 2 * nA + nV + nA + 2 * nU + 4 * nU)
     return graph + state
 
 
@@ -229,14 +231,14 @@ def topk_bytes(info, queries):
 
 
 # DRAM bytes (read + write) per tile-round of k_tiles on the medium graph, from
-# the ncu capture summarised in profiles/k_tiles_medium_tile32.md (373.61 GB over
+# the ncu capture summarised in profiles/k_tiles_medium_tile32.md (248.32 GB over
 # the 106 rounds of one 32-query tile).  It describes the kernel built from the
 # sources listed by hash; once any of them changes the figure no longer applies.
 NCU_TRAFFIC = {
     "graph": "medium",
-    "bytes_per_tile_round": 373.61e9 / 106,
-    "sources": {"ahpp_batch.cu": "5fc4c43e20957b74", "ahpp_batch.cuh": "f3dfbbd4287bd668",
-                "ahpp_internal.cuh": "5d60c05c7f5e231d"},
+    "bytes_per_tile_round": 248.32e9 / 106,
+    "sources": {"ahpp_batch.cu": "24d268b83918a951", "ahpp_batch.cuh": "f3dfbbd4287bd668",
+                "ahpp_internal.cuh": "baff201bb1863a8a"},
 }
 
 
@@ -252,6 +254,35 @@ def ncu_traffic(graph, tile_rounds):
             if hashlib.sha256(f.read()).hexdigest()[:16] != want:
                 return None
     return NCU_TRAFFIC["bytes_per_tile_round"] * tile_rounds
+
+
+def row_roofline(ahpp, info, tile_rounds, launch_s, device):
+    """The batched launch against the L2 row-access ceiling of this GPU.
+
+    Per tile-round the kernel gathers |E| residue rows (phase 1, from the
+    tile's |U| x 128-byte residue table), |E| t_V rows and |E_A| t_A rows
+    (phase 2), and reduces |E_A| rows into the next round's t_A (the attribute
+    push).  The ceiling is the time those row accesses take at the rates
+    ahpp_row_access_peak measures for tables of the same sizes; frac is that
+    time over the measured launch time (the streamed graph and state bytes
+    are left out of the ceiling, so frac is an upper estimate of the gap).
+    """
+    nU, nV, nA, nE, nEA = (int(info[k]) for k in ("n_u", "n_v", "n_a", "n_e", "n_ea"))
+    row = 4 * int(info["batch_tile"])
+    parts = [("gather", nU * row, nE, "phase 1: residue rows"),
+             ("gather", nV * row, nE, "phase 2: t_V rows"),
+             ("gather", nA * row, nEA, "phase 2: t_A rows"),
+             ("reduce", nA * row, nEA, "phase 2: attribute push into t_A")]
+    rates, t_min = [], 0.0
+    for op, table, n, what in parts:
+        r = ahpp.row_access_peak(table, op, device)
+        rates.append({"what": what, "op": op, "table_bytes": table, "rows_per_tile_round": n,
+                      "peak_rows_per_s": r})
+        t_min += n / r
+    rows = tile_rounds * sum(p[2] for p in parts)
+    return {"bound": "l2 row access", "unit": "rows/s",
+            "achieved": rows / launch_s, "peak": rows / (tile_rounds * t_min),
+            "frac": tile_rounds * t_min / launch_s, "rows_per_launch": rows, "parts": rates}
 
 
 # ------------------------------------------------------------ multi-rank
@@ -402,6 +433,11 @@ def run_ours(args, rank, world, local_rank):
             "kernel": "k_tiles (persistent: all rounds + top-k of one 1,024-query step)",
             "algorithmic_bytes_per_launch": alg,
             "tile_rounds_per_launch": tile_rounds}
+
+    try:
+        roof["l2_rows"] = row_roofline(ahpp, info, tile_rounds, sum(launch_ms) / K / 1e3, local_rank)
+    except Exception as e:  # the HBM roofline above stands on its own
+        roof["l2_rows"] = {"error": str(e)}
 
     lat_ms = launch_ms
     out = {

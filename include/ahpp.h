@@ -158,6 +158,17 @@ int ahpp_query(ahpp_graph *g, uint32_t q, double eps, uint32_t k,
  * indexed by the caller's U ids. */
 int ahpp_query_dense(ahpp_graph *g, uint32_t q, double eps, float *out_pi, ahpp_stats *st);
 
+/* Power Iteration (Algorithm 1) from q for T iterations, on the GPU:
+ * out_pi[n_u] (host, caller's U ids) receives Algorithm 1's iterate
+ * pi_T = alpha sum_{l<T} (1-alpha)^l e_q P^l + (1-alpha)^T e_q P^T, whose
+ * distance to the exact AHPP vector (Eq. 3) is at most (1-alpha)^T in every
+ * entry (FP32 arithmetic, Kahan-compensated sums).  It runs T synchronous
+ * push rounds from e_q (every positive residue pushed each round) and adds
+ * the final residues to the reserves.  A reference for graphs too large for
+ * a CPU solve.  st (nullable): rounds = T, mass sums of the push.
+ * AHPP_EINVAL for q outside U, T == 0 or T > 100000, NULL g or out_pi. */
+int ahpp_power_iteration(ahpp_graph *g, uint32_t q, uint32_t T, float *out_pi, ahpp_stats *st);
+
 /* n independent queries (q[i], eps[i], k[i]) pushed together: queries are
  * packed into tiles of 32 or 64 that share every read of the graph, and one
  * persistent launch runs all tiles.  Host inputs q[n], eps[n], k[n].  Host
@@ -239,6 +250,18 @@ int ahpp_server_info_get(ahpp_server *s, ahpp_server_info *info);
 /* Stop the loop, drop queued requests, release the slots and the server.
  * Safe on NULL.  No other call on s may run concurrently or follow. */
 int ahpp_server_stop(ahpp_server *s);
+
+/* Row-access peak of a device, for roofline reporting (no graph needed).
+ * The batched kernel moves its data as random 128-byte rows (32 queries x
+ * FP32 of one node); once a table fits in L2 the L2 -> SM path, not HBM,
+ * bounds those accesses.  This measures the rate, in rows per second, of
+ * random 128-byte row gathers from (op 0) or float4 row reductions into
+ * (op 1) a zero-filled device table of table_bytes (rounded down to 128-byte
+ * rows), best of five launches after a warm-up.  Allocates and frees the
+ * table itself and restores the caller's current device.  AHPP_EINVAL for
+ * op not 0/1, table_bytes outside [128, 8 GiB], device < 0 or a NULL output;
+ * AHPP_ENOMEM if the table cannot be allocated; AHPP_ECUDA otherwise. */
+int ahpp_row_access_peak(int device, uint64_t table_bytes, int op, double *rows_per_s);
 
 #ifdef __cplusplus
 }

@@ -109,6 +109,10 @@ SIGNATURES = {
                                  ctypes.POINTER(Stats)]),
     "ahpp_server_info_get": (ctypes.c_int, [_vp, ctypes.POINTER(ServerInfo)]),
     "ahpp_server_stop": (ctypes.c_int, [_vp]),
+    "ahpp_power_iteration": (ctypes.c_int, [_vp, ctypes.c_uint32, ctypes.c_uint32, _f32p,
+                                            ctypes.POINTER(Stats)]),
+    "ahpp_row_access_peak": (ctypes.c_int, [ctypes.c_int, ctypes.c_uint64, ctypes.c_int,
+                                            ctypes.POINTER(ctypes.c_double)]),
 }
 
 
@@ -236,6 +240,13 @@ class Graph:
                     (AHPP_ENOTCONVERGED,))
         return out, st.as_dict(), rc
 
+    def power_iteration(self, q: int, T: int):
+        """Algorithm 1's iterate after T iterations from q (dense, caller ids)."""
+        out = np.zeros(self.n_u, np.float32)
+        st = Stats()
+        rc = _check(lib().ahpp_power_iteration(self._h, q, T, _p(out, _f32p), ctypes.byref(st)))
+        return out, st.as_dict(), rc
+
     def query_batch(self, q, eps, k):
         q = np.ascontiguousarray(q, np.uint32)
         n = q.shape[0]
@@ -296,6 +307,15 @@ class Graph:
 
 
 STATS_BYTES = ctypes.sizeof(Stats)
+
+
+def row_access_peak(table_bytes: int, op: str = "gather", device: int = 0) -> float:
+    """Random 128-byte row gathers (op "gather") or float4 row reductions
+    (op "reduce") per second on `device`, from / into a table of table_bytes."""
+    out = ctypes.c_double(0.0)
+    _check(lib().ahpp_row_access_peak(device, int(table_bytes), {"gather": 0, "reduce": 1}[op],
+                                      ctypes.byref(out)))
+    return out.value
 
 
 class Server:

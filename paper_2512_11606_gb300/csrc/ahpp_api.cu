@@ -23,6 +23,8 @@ int cuda_fail(cudaError_t e, const char* where) {
 
 namespace {
 
+constexpr uint32_t kMaxPowerIterations = 100000;
+
 __global__ void k_scatter_dense(const float* __restrict__ pi, const uint32_t* __restrict__ n2o,
                                 uint32_t n, float* __restrict__ out) {
   for (uint32_t u = blockIdx.x * blockDim.x + threadIdx.x; u < n; u += gridDim.x * blockDim.x)
@@ -426,6 +428,38 @@ static int finish_single(ahpp_graph* g, double eps, ahpp_stats* st) {
     st->served_ms = 0.0;
   }
   return status_code(ctl.status);
+}
+
+int ahpp_power_iteration(ahpp_graph* g, uint32_t q, uint32_t T, float* out_pi, ahpp_stats* st) {
+  if (!g || !out_pi) { set_error("null argument"); return AHPP_EINVAL; }
+  if (q >= g->n_u) { set_error("q is not a node of U"); return AHPP_EINVAL; }
+  if (T == 0 || T > kMaxPowerIterations) {
+    set_error("T must be in [1, " + std::to_string(kMaxPowerIterations) + "]");
+    return AHPP_EINVAL;
+  }
+  std::lock_guard<std::mutex> lock(g->mu);
+  AHPP_CUDA(cudaSetDevice(g->device));
+  GraphIo* io = io_of(g);
+  Q1Params p = q1_params(g, g->h_u_old2new[q], 1.0);
+  p.pi_mode = 1;
+  p.algo = kAlgoASRP;
+  p.eps_f = 0.0;
+  p.max_rounds = T;
+  p.trace_cap = 0;
+  AHPP_CUDA(cudaMemsetAsync(g->q1.bar, 0, sizeof(GridBarrier), g->stream));
+  int e = launch_query1(g->dg, g->q1, p, g->bf16, g->q1_grid, g->stream);
+  if (e) return cuda_fail((cudaError_t)e, "power iteration launch");
+  int rc;
+  if ((rc = ensure(g, io->dense, 4ull * g->n_u))) return rc;
+  k_scatter_dense<<<std::max<int>(1, g->sm_count * 4), 256, 0, g->stream>>>(
+      g->q1.pi, g->d_u_new2old, (uint32_t)g->n_u, (float*)io->dense.p);
+  AHPP_CUDA(cudaGetLastError());
+  AHPP_CUDA(cudaMemcpyAsync(out_pi, io->dense.p, 4ull * g->n_u, cudaMemcpyDeviceToHost, g->stream));
+  rc = finish_single(g, 1.0, st);
+  // T rounds are the stopping rule here, not a cap that was hit
+  if (rc == AHPP_ENOTCONVERGED) rc = AHPP_OK;
+  if (st && rc == AHPP_OK) { st->status = 0; st->eps_f = 0.0; }
+  return rc;
 }
 
 int ahpp_query(ahpp_graph* g, uint32_t q, double eps, uint32_t k, uint32_t* out_nodes,

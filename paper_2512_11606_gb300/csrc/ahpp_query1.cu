@@ -84,7 +84,7 @@ __device__ void phase1(const Ctx& c, Partials& part) {
       } else {
         for (uint32_t k = item.z + lane; k < item.w; k += 32) {
           uint32_t u = idx[base + k];
-          s = fmaf(g.au_c[base + k], pushed(c.s.r_u, u), s);
+          s = fmaf(wload<WA>(g.au_w, base + k) * g.rnorm_u[u], pushed(c.s.r_u, u), s);
         }
       }
       s = warp_sum(s);
@@ -113,7 +113,7 @@ __device__ void phase1(const Ctx& c, Partials& part) {
       } else {
         for (uint32_t k = b; k < e; ++k) {
           uint32_t u = idx[k];
-          s = fmaf(g.au_c[k], pushed(c.s.r_u, u), s);
+          s = fmaf(wload<WA>(g.au_w, k) * g.rnorm_u[u], pushed(c.s.r_u, u), s);
         }
       }
       p1_epilogue(c, is_a, row, s, part);
@@ -377,7 +377,7 @@ k_query1(const __grid_constant__ DevGraph g, const __grid_constant__ Q1State s,
   }
   if (!grid_sync(s.bar, nb)) return;
 
-  int phase = p.lambda_mode ? kPhaseSync : kPhaseAsync;
+  int phase = (p.lambda_mode || p.pi_mode) ? kPhaseSync : kPhaseAsync;
   int status = kStatusOk;
   int dense = p.lambda_mode ? 1 : 0;
   uint32_t rounds = 0, switch_round = 0, dense_rounds = 0;
@@ -448,9 +448,9 @@ k_query1(const __grid_constant__ DevGraph g, const __grid_constant__ Q1State s,
     float mr = 0.f, mp = 0.f;
     for (uint32_t u = c.gt; u < g.n_u; u += c.nt) {
       const float v = fmaxf(s.pi[u] - s.pic[u], 0.f);
-      s.pi[u] = v;
-      s.pic[u] = 0.f;
       const float r = fabsf(s.r_u[u]);
+      s.pi[u] = p.pi_mode ? v + r : v;
+      s.pic[u] = 0.f;
       sp += v; sr += r; mr = fmaxf(mr, r); mp = fmaxf(mp, v);
     }
     sp = warp_sum_d(sp); sr = warp_sum_d(sr); mr = warp_max(mr); mp = warp_max(mp);

@@ -36,6 +36,10 @@ struct Q1Params {
   // synchronous rounds; the reserves are then pi_T and final_maxr_bits[1]
   // holds max_u pi_T(u).
   int lambda_mode = 0;
+  // Algorithm 1 mode: start from r = e_q in the synchronous phase (every
+  // positive residue pushed each round) and run exactly max_rounds rounds;
+  // the output is then reserves + residues, Algorithm 1's iterate.
+  int pi_mode = 0;
 };
 
 int launch_query1(const DevGraph& g, const Q1State& s, const Q1Params& p, bool bf16, int grid,

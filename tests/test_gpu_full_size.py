@@ -74,6 +74,16 @@ def test_medium_single_and_batched_vs_oracle(medium):
         assert s["max_resid"] <= s["eps_f"] * (1 + 1e-6)
         assert s["eps_f"] <= eps / lam * (1 + 1e-6)
 
+    # the eps guarantee of Theorem 2 against the GPU's Algorithm 1 at T = 250
+    # ((1 - alpha)^250 < 1e-17): 0 <= pi - pi_hat <= eps, up to FP32 rounding
+    for i in (0, 63):
+        pi_T, _, rc = G.power_iteration(qs[i], 250)
+        assert rc == 0
+        d = pi_T.astype(np.float64) - dense[i].astype(np.float64)
+        assert d.min() >= -5e-7 and d.max() <= eps + 5e-7
+        if i == 0:
+            assert np.abs(pi_T.astype(np.float64) - ref.pi).max() <= eps + TOL
+
     # the launch bench.py times: 1,024 queries, top-100 each
     k = 100
     res = G.query_batch(q1024, eps, k)
@@ -111,5 +121,10 @@ def test_large_graph_properties(ahpp):
         assert top.nodes.shape[0] == 1000
         np.testing.assert_allclose(top.scores, alone[top.nodes], rtol=1e-5, atol=TOL)
         assert abs(res[0].stats["rounds"] - st["rounds"]) <= 1
+        # Theorem 2 against the GPU's Algorithm 1 at T = 250
+        pi_T, _, rc = G.power_iteration(qs[0], 250)
+        assert rc == 0
+        d = pi_T.astype(np.float64) - alone.astype(np.float64)
+        assert d.min() >= -5e-7 and d.max() <= eps + 5e-7
     finally:
         G.close()

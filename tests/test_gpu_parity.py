@@ -281,3 +281,36 @@ def test_round_cap_reports_not_converged(ahpp, tiny):
         assert np.abs(pi - ref.pi).max() <= TOL
     finally:
         G.close()
+
+
+@pytest.mark.parametrize("T", [1, 2, 10, 60])
+def test_power_iteration_matches_oracle(tiny, T):
+    """Algorithm 1 on the GPU: the oracle's iterate after T steps, and within
+    (1 - alpha)^T of exact AHPP."""
+    G, og = tiny["G"], tiny["og"]
+    for q in tiny["qs"][:2]:
+        pi_gpu, st, rc = G.power_iteration(q, T)
+        assert rc == 0 and st["rounds"] == T
+        ref = og.power_iteration(ALPHA, BETA, q, T)
+        assert np.abs(pi_gpu.astype(np.float64) - ref).max() <= TOL
+        assert np.abs(tiny["Pi"][q] - pi_gpu).max() <= (1 - ALPHA) ** T + TOL
+        assert abs(pi_gpu.astype(np.float64).sum() - 1.0) <= 1e-5
+
+
+def test_power_iteration_one_step_closed_form(tiny):
+    """T = 1: alpha e_q + (1 - alpha) e_q P, with P from its definition."""
+    G, g = tiny["G"], tiny["g"]
+    _, _, P = oracle.dense_matrices_of(g, BETA)
+    q = tiny["qs"][1]
+    pi_gpu, _, _ = G.power_iteration(q, 1)
+    want = (1 - ALPHA) * P[q]
+    want[q] += ALPHA
+    assert np.abs(pi_gpu - want).max() <= 1e-7
+
+
+def test_power_iteration_invalid(ahpp, tiny):
+    G = tiny["G"]
+    for q, T in [(0, 0), (tiny["g"].n_u, 5), (0, 100001)]:
+        with pytest.raises(ahpp.AhppError) as e:
+            G.power_iteration(q, T)
+        assert e.value.code == ahpp.AHPP_EINVAL
