@@ -1,0 +1,182 @@
+"""The remaining public paths of the C ABI against the host paths and the oracle.
+
+Device-resident calls (the launch bench.py times), the ASRP switch rules,
+concurrent tile groups and the autotuner, APP in the batched kernel, and the
+batch edge cases (empty batch, k clamped to |U|).
+"""
+import ctypes
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2512_11606_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+ALPHA, BETA = 0.15, 0.35
+TOL = 1e-6
+
+
+@pytest.fixture(scope="module")
+def ahpp():
+    from paper_2512_11606_gb300 import build
+    build.build()
+    from paper_2512_11606_gb300 import ahpp as mod
+    return mod
+
+
+@pytest.fixture(scope="module")
+def tiny(ahpp):
+    g = synth.make_graph(**synth.TINY)
+    og = oracle.OracleGraph.from_arrays(g)
+    lam, _ = og.lambda_estimate(ALPHA, BETA)
+    G = ahpp.Graph.from_arrays(g, lam=lam, attr_bf16=0)
+    yield dict(g=g, og=og, lam=lam, G=G)
+    G.close()
+
+
+def stats_of(ahpp, raw):
+    """Decode a [n, sizeof(ahpp_stats)] byte tensor into dicts."""
+    n = raw.shape[0]
+    buf = (ahpp.Stats * n).from_buffer_copy(raw.cpu().numpy().tobytes())
+    return [buf[i].as_dict() for i in range(n)]
+
+
+def test_device_batch_matches_host(ahpp, tiny):
+    torch = pytest.importorskip("torch")
+    G, g = tiny["G"], tiny["g"]
+    n, kmax = 45, 50
+    qs = synth.draw_queries(g.n_u, n, seed=71).astype(np.int64)
+    ks = np.where(np.arange(n) % 2 == 0, 50, 13)
+    dev = torch.device("cuda", 0)
+    q_t = torch.tensor(qs, dtype=torch.int32, device=dev)
+    eps_t = torch.full((n,), 1e-6, dtype=torch.float64, device=dev)
+    k_t = torch.tensor(ks, dtype=torch.int32, device=dev)
+    nodes_t = torch.full((n, kmax), -1, dtype=torch.int32, device=dev)
+    scores_t = torch.zeros((n, kmax), dtype=torch.float32, device=dev)
+    n_t = torch.zeros(n, dtype=torch.int32, device=dev)
+    st_t = torch.zeros((n, ahpp.STATS_BYTES), dtype=torch.uint8, device=dev)
+    stream = torch.cuda.Stream(device=dev)
+    rc = G.query_batch_device(q_t, eps_t, k_t, kmax, nodes_t, scores_t, n_t, st_t, stream)
+    stream.synchronize()
+    assert rc == 0
+    host = G.query_batch([int(x) for x in qs], 1e-6, ks.astype(np.uint32))
+    dst = stats_of(ahpp, st_t)
+    cnt = n_t.cpu().numpy()
+    nodes = nodes_t.cpu().numpy()
+    scores = scores_t.cpu().numpy()
+    for i in range(n):
+        assert cnt[i] == ks[i]
+        h = host[i]
+        common = len(set(nodes[i, :cnt[i]].tolist()) & set(h.nodes.tolist())) / ks[i]
+        assert common >= 0.98
+        hs = dict(zip(h.nodes.tolist(), h.scores.tolist()))
+        for v, s in zip(nodes[i, :cnt[i]].tolist(), scores[i, :cnt[i]].tolist()):
+            if v in hs:
+                assert abs(s - hs[v]) <= TOL
+        assert dst[i]["rounds"] == h.stats["rounds"] and dst[i]["status"] == 0
+        assert dst[i]["mass_err"] < 1e-5
+
+
+def test_device_single_matches_host(ahpp, tiny):
+    torch = pytest.importorskip("torch")
+    G, g = tiny["G"], tiny["g"]
+    dev = torch.device("cuda", 0)
+    k = 40
+    nodes_t = torch.zeros(k, dtype=torch.int32, device=dev)
+    scores_t = torch.zeros(k, dtype=torch.float32, device=dev)
+    n_t = torch.zeros(1, dtype=torch.int32, device=dev)
+    st_t = torch.zeros((1, ahpp.STATS_BYTES), dtype=torch.uint8, device=dev)
+    for q in synth.draw_queries(g.n_u, 3, seed=72):
+        rc = G.query_device(int(q), 1e-6, k, nodes_t, scores_t, n_t, st_t, None)
+        torch.cuda.synchronize()
+        assert rc == 0
+        h = G.query(int(q), 1e-6, k)
+        assert int(n_t.item()) == k
+        np.testing.assert_allclose(scores_t.cpu().numpy(), h.scores, atol=TOL)
+        assert stats_of(ahpp, st_t)[0]["rounds"] == h.stats["rounds"]
+
+
+@pytest.mark.parametrize("rule", [1, 2])
+def test_switch_rules_match_oracle(ahpp, tiny, rule):
+    """switch_rule 1 (the printed formula) and 2 (never switch): single and
+    batched results follow the oracle run with the same rule."""
+    g, og, lam = tiny["g"], tiny["og"], tiny["lam"]
+    G = ahpp.Graph.from_arrays(g, lam=lam, attr_bf16=0, switch_rule=rule)
+    try:
+        qs = [int(x) for x in synth.draw_queries(g.n_u, 3, seed=73)]
+        dense, stats, rc = G.query_batch_dense(qs, 1e-6)
+        assert rc == 0
+        for i, q in enumerate(qs):
+            ref = og.push("asrp", ALPHA, BETA, q, 1e-6, lam=lam, switch_rule=rule)
+            one, st, rc1 = G.query_dense(q, 1e-6)
+            assert rc1 == 0
+            assert np.abs(one.astype(np.float64) - ref.pi).max() <= TOL
+            assert np.abs(dense[i].astype(np.float64) - ref.pi).max() <= TOL
+            assert abs(st["rounds"] - ref.stats["rounds"]) <= 1
+            if rule == 2:
+                assert st["switch_round"] == 0 and ref.stats["switch_round"] == 0
+    finally:
+        G.close()
+
+
+@pytest.mark.parametrize("groups", [2, 4])
+def test_concurrent_tile_groups_same_results(ahpp, tiny, groups):
+    g, lam = tiny["g"], tiny["lam"]
+    qs = [int(x) for x in synth.draw_queries(g.n_u, 150, seed=74)]
+    base, st0, _ = tiny["G"].query_batch_dense(qs, 1e-6)
+    G = ahpp.Graph.from_arrays(g, lam=lam, attr_bf16=0, batch_groups=groups)
+    try:
+        assert G.info["batch_groups"] == groups
+        dense, st, rc = G.query_batch_dense(qs, 1e-6)
+        assert rc == 0
+        assert np.abs(dense - base).max() <= TOL
+        assert [s["rounds"] for s in st] == [s["rounds"] for s in st0]
+    finally:
+        G.close()
+
+
+def test_autotune_keeps_results(ahpp, tiny):
+    g, lam = tiny["g"], tiny["lam"]
+    G = ahpp.Graph.from_arrays(g, lam=lam, attr_bf16=0)
+    try:
+        qs = [int(x) for x in synth.draw_queries(g.n_u, 64, seed=75)]
+        before, _, _ = G.query_batch_dense(qs, 1e-6)
+        info = G.autotune(qs, 1e-6)
+        assert info["batch_groups"] in (1, 2, 4)
+        after, _, rc = G.query_batch_dense(qs, 1e-6)
+        assert rc == 0 and np.abs(after - before).max() <= TOL
+    finally:
+        G.close()
+
+
+def test_batched_app_matches_oracle(ahpp, tiny):
+    g, og = tiny["g"], tiny["og"]
+    G = ahpp.Graph.from_arrays(g, algo=ahpp.AHPP_APP, attr_bf16=0)
+    try:
+        qs = [int(x) for x in synth.draw_queries(g.n_u, 35, seed=76)]
+        eps = np.where(np.arange(35) % 2 == 0, 1e-6, 1e-4)
+        dense, stats, rc = G.query_batch_dense(qs, eps)
+        assert rc == 0
+        for i in [0, 1, 17, 33, 34]:
+            ref = og.push("app", ALPHA, BETA, qs[i], float(eps[i]))
+            tol = max(TOL, float(eps[i]))
+            assert np.abs(dense[i].astype(np.float64) - ref.pi).max() <= tol
+            assert abs(stats[i]["rounds"] - ref.stats["rounds"]) <= 1
+            one, _, _ = G.query_dense(qs[i], float(eps[i]))
+            assert np.abs(one - dense[i]).max() <= TOL
+    finally:
+        G.close()
+
+
+def test_empty_batch_and_k_clamped(ahpp, tiny):
+    G, g = tiny["G"], tiny["g"]
+    assert G.query_batch([], 1e-6, 10) == []
+    res = G.query_batch([3, 5], 1e-4, ahpp.AHPP_MAX_K)
+    for r in res:
+        assert r.nodes.shape[0] == g.n_u
+        assert sorted(r.nodes.tolist()) == list(range(g.n_u))
+        assert np.all(np.diff(r.scores) <= 0)
+    with pytest.raises(ahpp.AhppError) as e:
+        G.query_batch([3], 1e-6, ahpp.AHPP_MAX_K + 1)
+    assert e.value.code == ahpp.AHPP_EINVAL
