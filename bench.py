@@ -51,7 +51,9 @@ def parse(argv=None):
     ap.add_argument("--cpu-queries", type=int, default=0, help="0: one per host core (max 16)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--graph", default="medium", choices=["medium", "tiny"])
+    ap.add_argument("--graph", default="medium", choices=["medium", "tiny", "large"])
+    ap.add_argument("--ablation", type=int, default=0,
+                    help="single-query ablation of the ASRP switch rule and APP on N queries (0: off)")
     ap.add_argument("--serve-seconds", type=float, default=12.0,
                     help="open-loop serving window (0 disables the serving measurement)")
     ap.add_argument("--serve-load", type=float, default=0.8,
@@ -62,6 +64,8 @@ def parse(argv=None):
 
 
 def graph_spec(name):
+    if name == "large":
+        return dict(synth.LARGE)
     return dict(synth.MEDIUM_BF16) if name == "medium" else dict(synth.TINY, bf16=True)
 
 
@@ -77,7 +81,10 @@ def workload_config(args, extra=None):
         "batch_queries_per_gpu": args.batch,
         "eps": args.eps,
         "k": args.k,
-        "l2": "inputs larger than L2 (graph ~0.7 GB + per-tile state ~0.45 GB per round)",
+        "l2": ("inputs larger than L2 (graph ~0.7 GB + per-tile state ~0.45 GB per round)"
+               if args.graph == "medium" else
+               "inputs larger than L2 (graph ~5 GB + per-tile state ~2.3 GB per round)"
+               if args.graph == "large" else "tiny graph: L2-resident, reported, not graded"),
         "parallelism": f"replicas{args.gpus}" if args.gpus > 1 else "1 GPU",
     }
     if extra:
@@ -421,6 +428,10 @@ def run_ours(args, rank, world, local_rank):
     if rank == 0 and args.serve_seconds > 0:
         served = run_serving(ahpp, G, g, args, rate=args.serve_load * value / world)
 
+    ablation = None
+    if rank == 0 and args.ablation > 0:
+        ablation = run_ablation(ahpp, g, args, info["lambda"], local_rank)
+
     # roofline of the dominant kernel (the batched persistent launch)
     peak, peak_kind = measured_peak()
     alg = tile_rounds * round_bytes(info, tile) + topk_bytes(info, B)   # one launch (last step)
@@ -467,6 +478,7 @@ def run_ours(args, rank, world, local_rank):
         "not_converged": int((stats["status"] != 0).sum()),
         "mass_err_max": float(stats["mass_err"].max()),
         "roofline": roof,
+        "ablation": ablation,
         "cpu_baseline": cpu and {k: cpu[k] for k in ("value", "unit", "cores", "kind", "sample")},
         "e2e": e2e,
         "gpu_launches": K,
@@ -474,6 +486,41 @@ def run_ours(args, rank, world, local_rank):
         "wall_s": wall,
     }
     G.close()
+    return out
+
+
+def run_ablation(ahpp, g, args, lam, device):
+    """Single-query ablation on the same graph (Exp-2's question): ASRP with
+    the switch budget as read (rule 0), as printed (rule 1), never switching
+    (rule 2), and APP; per variant the mean rounds, switch round and the
+    plain-path throughput over args.ablation queries."""
+    import torch
+    variants = [("ASRP, switch budget as read (default)", dict(algo=ahpp.AHPP_ASRP, switch_rule=0)),
+                ("ASRP, switch budget as printed", dict(algo=ahpp.AHPP_ASRP, switch_rule=1)),
+                ("ASRP, never switch", dict(algo=ahpp.AHPP_ASRP, switch_rule=2)),
+                ("APP", dict(algo=ahpp.AHPP_APP))]
+    qs = synth.draw_queries(g.n_u, args.ablation + 1, seed=303)
+    dev = torch.device("cuda", device)
+    out = []
+    for name, cfg in variants:
+        G = ahpp.Graph.from_arrays(g, lam=lam, device=device, **cfg)
+        try:
+            G.query(int(qs[0]), args.eps, 1)                   # warm-up
+            rounds, sw, ms = [], [], []
+            for q in qs[1:]:
+                a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                a.record()
+                r = G.query(int(q), args.eps, args.k)
+                b.record()
+                torch.cuda.synchronize()
+                ms.append(a.elapsed_time(b))
+                rounds.append(r.stats["rounds"])
+                sw.append(r.stats["switch_round"])
+            out.append({"variant": name, "queries": len(ms), "qps": 1e3 / statistics.mean(ms),
+                        "p50_ms": statistics.median(ms), "rounds_mean": statistics.mean(rounds),
+                        "switch_round_mean": statistics.mean(sw)})
+        finally:
+            G.close()
     return out
 
 
