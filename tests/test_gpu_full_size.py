@@ -101,6 +101,42 @@ def test_medium_single_and_batched_vs_oracle(medium):
         assert dense[i][r.nodes].min() >= kth_i - 2 * TOL
 
 
+def test_medium_served_mix_equals_alone(ahpp, medium):
+    """Continuous batching at full size with the serving workload's request
+    mix (eps log-uniform in [1e-7, 1e-4], k in {10, 100, 1000}): requests
+    admitted while others run give the same result as the query alone, and
+    one of them is checked against the oracle."""
+    G, og, lam, g = medium["G"], medium["og"], medium["lam"], medium["g"]
+    rng = np.random.default_rng(17)
+    n = 48
+    qs = synth.draw_queries(g.n_u, n, seed=61)
+    eps = np.exp(rng.uniform(np.log(1e-7), np.log(1e-4), n))
+    ks = rng.choice([10, 100, 1000], n)
+    srv = ahpp.Server(G, max_slots=32, rounds_per_step=8)
+    try:
+        tickets = [srv.submit(int(qs[i]), float(eps[i]), int(ks[i])) for i in range(24)]
+        first = srv.wait(tickets[0], int(ks[0]))
+        tickets += [srv.submit(int(qs[i]), float(eps[i]), int(ks[i])) for i in range(24, n)]
+        results = [first] + [srv.wait(t, int(k)) for t, k in zip(tickets[1:], ks[1:])]
+        info = srv.info()
+        assert info["completed"] == n and info["steps"] > 1
+    finally:
+        srv.stop()
+    for i in [0, 5, 23, 24, 30, 47]:
+        r = results[i]
+        assert r.rc == 0 and r.stats["status"] == 0 and r.stats["mass_err"] < 1e-5
+        alone = G.query(int(qs[i]), float(eps[i]), int(ks[i]))
+        assert r.stats["rounds"] == alone.stats["rounds"]
+        common = len(set(r.nodes.tolist()) & set(alone.nodes.tolist())) / int(ks[i])
+        assert common >= 0.98
+        a = dict(zip(alone.nodes.tolist(), alone.scores.tolist()))
+        assert all(abs(sc - a[v]) <= TOL for v, sc in zip(r.nodes.tolist(), r.scores.tolist()) if v in a)
+    i = int(np.argmin(eps[:24]))                  # the tightest eps of the first wave
+    ref = og.push("asrp", ALPHA, BETA, int(qs[i]), float(eps[i]), lam=lam)
+    r = results[i]
+    assert np.abs(r.scores.astype(np.float64) - ref.pi[r.nodes]).max() <= TOL
+
+
 @pytest.mark.slow
 @pytest.mark.skipif(os.environ.get("AHPP_LARGE") != "1",
                     reason="large graph: about 3 minutes of host-side generation; set AHPP_LARGE=1")
