@@ -58,7 +58,7 @@ def parse(argv=None):
                     help="open-loop serving window (0 disables the serving measurement)")
     ap.add_argument("--serve-load", type=float, default=0.8,
                     help="Poisson arrival rate as a fraction of the measured batched capacity")
-    ap.add_argument("--serve-slots", type=int, default=64)
+    ap.add_argument("--serve-slots", type=int, default=32)
     ap.add_argument("--serve-rounds", type=int, default=4)
     return ap.parse_args(argv)
 
@@ -386,10 +386,12 @@ def run_ours(args, rank, world, local_rank):
     t_max = max_over_ranks(dev_s, world, dev)
     value = whole_job_value(world, B, K, t_max)
 
-    # e2e through the host API (pinned-free host numpy buffers, copies inside)
+    # e2e through the host API: each step's query ids come from pinned host
+    # memory, the library copies them in and the results out inside the call
     e2e = None
     if not args.no_e2e:
-        host_q = [qs_all[W + j] for j in range(K)]
+        pinned = torch.from_numpy(qs_all[W:].astype(np.int32)).pin_memory()
+        host_q = [pinned[j].numpy().view(np.uint32) for j in range(K)]
         G.query_batch(host_q[0][:64], args.eps, args.k)       # warm the host path
         torch.cuda.synchronize()
         te = time.perf_counter()
