@@ -777,6 +777,8 @@ k_tiles(const __grid_constant__ DevGraph g, const __grid_constant__ BatchState s
   __shared__ int s_new[kTile];       // serving: slot admitted at this step
   __shared__ int s_fin[kTile];       // lane finished: finalise and select top-k
   __shared__ uint32_t s_k[kTile];    // top-k size of the lane
+  __shared__ int s_pick_d[kTile];    // top-k: digit, keys above it and its count, per lane
+  __shared__ uint32_t s_pick_cum[kTile], s_pick_h[kTile];
   __shared__ int s_flag;
   __shared__ TileBuf s_tb;
 #if AHPP_TMA
@@ -1053,16 +1055,25 @@ k_tiles(const __grid_constant__ DevGraph g, const __grid_constant__ BatchState s
         if (p.out_stats) p.out_stats[qi] = S;
       }
 
-      // ---- top-k per lane: radix select over 64-bit (score, ~caller id) keys
+      // ---- top-k per lane: radix select over 64-bit (score, ~caller id) keys.
+      // A lane stops as soon as the bucket holding its k-th key contains
+      // exactly the keys it still needs (then every key of that bucket is a
+      // winner); with distinct scores that happens once the score bits are
+      // resolved, so the caller-id passes are skipped.
       if (kmax) {
         unsigned int* sh = reinterpret_cast<unsigned int*>(smem);    // [kTile][kRadixBins]
         unsigned long long prefix = 0;
+        unsigned long long thresh = 0;        // smallest winning key, once known
         uint32_t krem = kq;
+        bool known = kq == 0;
         for (int pass = 0; pass < kRadixPasses; ++pass) {
+          // every block holds the same per-lane state (read from the same
+          // global histograms), so all blocks leave the loop together
+          if (!__syncthreads_or(!known)) break;
           const int shift = 64 - kRadixBits * (pass + 1);
           for (int i = threadIdx.x; i < kTile * kRadixBins; i += kThreads) sh[i] = 0;
           __syncthreads();
-          if (krem) {
+          if (!known) {
             for (size_t u = c.gw; u < g.n_u; u += c.nw) {
               const unsigned long long key = score_key(tb.pi[u * kTile + lane], p.u_new2old[u]);
               if (pass == 0 || (key >> (shift + kRadixBits)) == prefix)
@@ -1074,23 +1085,35 @@ k_tiles(const __grid_constant__ DevGraph g, const __grid_constant__ BatchState s
           for (int i = threadIdx.x; i < kTile * kRadixBins; i += kThreads)
             if (sh[i]) atomicAdd(&gh[i], sh[i]);
           if (!grid_sync(tb.bar, nbg)) return;
-          if (krem) {
-            uint32_t cum = 0;
-            int d = kRadixBins - 1;
-            for (; d > 0; --d) {
-              const uint32_t h = __ldcg(&gh[lane * kRadixBins + d]);
-              if (cum + h >= krem) break;
-              cum += h;
-            }
+          // the merged histograms into shared memory; warp w picks the digit
+          // of queries w, w + 8, ... (warp-parallel), lane l reads query l's
+          for (int i = threadIdx.x; i < kTile * kRadixBins; i += kThreads) sh[i] = __ldcg(&gh[i]);
+          __syncthreads();
+          for (int l = threadIdx.x >> 5; l < kTile; l += kWarps) {
+            const uint32_t kr = __shfl_sync(kFull, krem, l);
+            if (__shfl_sync(kFull, (int)known, l)) continue;
+            int dd;
+            uint32_t cc, hh;
+            radix_pick(sh + l * kRadixBins, kRadixBins, kr, &dd, &cc, &hh);
+            if ((threadIdx.x & 31) == 0) { s_pick_d[l] = dd; s_pick_cum[l] = cc; s_pick_h[l] = hh; }
+          }
+          __syncthreads();
+          if (!known) {
+            const int d = s_pick_d[lane];
+            const uint32_t cum = s_pick_cum[lane], h = s_pick_h[lane];
             krem -= cum;
             prefix = (prefix << kRadixBits) | (unsigned long long)d;
+            if (h == krem || shift == 0) {
+              known = true;
+              thresh = prefix << shift;
+            }
           }
         }
-        // prefix is the exact key of the kq-th largest; keys are distinct
+        // the lane's winners are exactly its keys >= thresh (keys are distinct)
         if (kq) {
           for (size_t u = c.gw; u < g.n_u; u += c.nw) {
             const unsigned long long key = score_key(tb.pi[u * kTile + lane], p.u_new2old[u]);
-            if (key >= prefix) {
+            if (key >= thresh) {
               const uint32_t pos = atomicAdd(&tb.cand_cnt[lane], 1u);
               if (pos < kmax) tb.cand[(size_t)lane * kmax + pos] = key;
             }

@@ -172,6 +172,44 @@ __device__ __forceinline__ bool grid_sync(GridBarrier* b, unsigned int nblocks) 
 
 // ------------------------------------------------------------ reductions
 
+// Radix-select step on a histogram in shared memory (bins a power of two >= 32):
+// the largest digit d such that the keys in buckets above d plus hist[d]
+// reach krem.  Warp-collective: lane L sums bins [L*bins/32, (L+1)*bins/32),
+// a suffix sum over the lanes and a ballot find the lane holding the
+// crossing, and that lane walks its own bins.  Every lane receives d, cum
+// (keys in the buckets above d) and h = hist[d].
+__device__ __forceinline__ void radix_pick(const unsigned int* hist, int bins, uint32_t krem, int* d_out,
+                                           uint32_t* cum_out, uint32_t* h_out) {
+  const int lane = threadIdx.x & 31;
+  const int per = bins >> 5;
+  const unsigned int* mine = hist + lane * per;
+  uint32_t sum = 0;
+  for (int j = 0; j < per; ++j) sum += mine[(j + lane) & (per - 1)];   // rotated: fewer bank conflicts
+  uint32_t suf = sum;                                   // keys in lanes >= lane
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const uint32_t t = __shfl_down_sync(0xffffffffu, suf, o);
+    if (lane + o < 32) suf += t;
+  }
+  const unsigned int ball = __ballot_sync(0xffffffffu, suf >= krem);
+  const int L = ball ? 31 - __clz(ball) : 0;
+  int d = 0;
+  uint32_t cum = 0, h = 0;
+  if (lane == L) {
+    cum = suf - sum;                                    // keys in the lanes above L
+    int j = per - 1;
+    for (; j >= 0; --j) {
+      h = mine[j];
+      if (cum + h >= krem || j == 0) break;
+      cum += h;
+    }
+    d = L * per + j;
+  }
+  *d_out = __shfl_sync(0xffffffffu, d, L);
+  *cum_out = __shfl_sync(0xffffffffu, cum, L);
+  *h_out = __shfl_sync(0xffffffffu, h, L);
+}
+
 __device__ __forceinline__ float warp_sum(float v) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);

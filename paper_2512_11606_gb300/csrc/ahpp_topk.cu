@@ -1,8 +1,9 @@
 // Top-k of one reserve vector: radix select over distinct 64-bit keys
 // (score bits << 32 | ~caller id), so that the k largest keys are exactly the
-// k best nodes ordered by score descending, then caller id ascending.  Six
-// passes of 11/11/10 bits pin down the k-th key; the k winners are then
-// gathered and sorted in one block (bitonic, k <= AHPP_MAX_K).
+// k best nodes ordered by score descending, then caller id ascending.  Up to
+// six passes of 11/11/10 bits narrow down the k-th key (usually the three
+// score passes suffice); the k winners are then gathered and sorted in one
+// block (bitonic, k <= AHPP_MAX_K).
 #include "ahpp_host.h"
 
 namespace ahpp {
@@ -37,8 +38,12 @@ k_topk1(const float* __restrict__ score, const uint32_t* __restrict__ n2o, uint3
   if (gt == 0) *sc.cand_cnt = 0;
   if (!grid_sync(sc.bar, nb)) return;
   unsigned long long prefix = 0;
+  unsigned long long thresh = 0;   // smallest winning key, once known
   uint32_t krem = k;
   int done_bits = 0;
+  // Every block reads the same global histograms, so all blocks stop after
+  // the same pass: as soon as the bucket holding the k-th key contains
+  // exactly the keys still needed, all of that bucket wins.
   for (int pass = 0; pass < kPasses; ++pass) {
     const int bits = c_bits[pass];
     const int bins = 1 << bits;
@@ -55,21 +60,25 @@ k_topk1(const float* __restrict__ score, const uint32_t* __restrict__ n2o, uint3
     for (int i = threadIdx.x; i < bins; i += kThreads)
       if (sh[i]) atomicAdd(&gh[i], sh[i]);
     if (!grid_sync(sc.bar, nb)) return;
-    uint32_t cum = 0;
-    int d = bins - 1;
-    for (; d > 0; --d) {
-      const uint32_t h = __ldcg(&gh[d]);
-      if (cum + h >= krem) break;
-      cum += h;
-    }
+    // the merged histogram into shared memory, then a warp-parallel pick
+    for (int i = threadIdx.x; i < bins; i += kThreads) sh[i] = __ldcg(&gh[i]);
+    __syncthreads();
+    int d;
+    uint32_t cum, h;
+    radix_pick(sh, bins, krem, &d, &cum, &h);
+    __syncthreads();
     krem -= cum;
     prefix = (prefix << bits) | (unsigned long long)d;
     done_bits += bits;
+    if (h == krem || done_bits == 64) {
+      thresh = prefix << (64 - done_bits);
+      break;
+    }
   }
-  // prefix is the key of the k-th largest; exactly k keys are >= prefix
+  // exactly k keys are >= thresh (keys are distinct)
   for (uint32_t u = gt; u < n; u += nt) {
     const unsigned long long key = key_of(score, n2o, u);
-    if (key >= prefix) {
+    if (key >= thresh) {
       const uint32_t pos = atomicAdd(sc.cand_cnt, 1u);
       if (pos < AHPP_MAX_K) sc.cand[pos] = key;
     }
