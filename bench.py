@@ -545,11 +545,13 @@ def run_serving(ahpp, G, g, args, rate):
         for t in warm:
             srv.wait(t, args.k)
 
-        # saturated (closed loop)
+        # saturated (closed loop): every slot busy plus a small queued backlog,
+        # so that a slot freed at a step is refilled at the next step
         n_sat = max(4 * slots, int(args.serve_seconds * rate / max(args.serve_load, 1e-3) / 2))
+        inflight = slots + max(4, slots // 4)
         qs = synth.draw_queries(g.n_u, n_sat, seed=202)
-        pending = [srv.submit(int(q), args.eps, args.k) for q in qs[:slots]]
-        nxt = slots
+        pending = [srv.submit(int(q), args.eps, args.k) for q in qs[:inflight]]
+        nxt = inflight
         done_t, lat = [], []
         t0 = time.perf_counter()
         while pending:
@@ -559,14 +561,15 @@ def run_serving(ahpp, G, g, args, rate):
             if nxt < n_sat:
                 pending.append(srv.submit(int(qs[nxt]), args.eps, args.k))
                 nxt += 1
-        lo, hi = slots, n_sat - slots          # steady state: after the first wave, before the drain
+        lo, hi = inflight, n_sat - inflight    # steady state: after the first wave, before the drain
         if hi - lo >= 8:
             out["saturated"] = {
                 "qps": (hi - lo) / (done_t[hi - 1] - done_t[lo - 1]),
                 "p50_ms": statistics.median(lat[lo:hi]),
                 "p99_ms": float(np.percentile(lat[lo:hi], 99)),
                 "queries": n_sat, "window_queries": hi - lo,
-                "note": "closed loop, requests in flight = slots; qps over the steady-state window",
+                "in_flight": inflight,
+                "note": "closed loop, requests in flight = slots + a queued backlog; qps over the steady-state window",
             }
 
         # open loop (Poisson arrivals)
