@@ -81,8 +81,8 @@ typedef struct {
     uint64_t hbm_budget_bytes; /* cap on device memory of graph + query state; 0 = no cap */
     int device;                /* CUDA device ordinal (default 0) */
     uint32_t max_rounds;       /* round cap per query; 0: automatic */
-    uint32_t batch_tile;       /* queries per batched tile: 32 or 64; 0: autotuned/default 32 */
-    uint32_t batch_groups;     /* tiles processed concurrently: 1, 2 or 4; 0: autotuned/default 1 */
+    uint32_t batch_tile;       /* queries per batched tile: 0 or 32 (the width the library is built for) */
+    uint32_t batch_groups;     /* tiles processed concurrently, 1..8; 0: 1 (ahpp_autotune picks 1, 2 or 4) */
 } ahpp_config;
 
 /* Per-query statistics. */
@@ -170,7 +170,7 @@ int ahpp_query_dense(ahpp_graph *g, uint32_t q, double eps, float *out_pi, ahpp_
 int ahpp_power_iteration(ahpp_graph *g, uint32_t q, uint32_t T, float *out_pi, ahpp_stats *st);
 
 /* n independent queries (q[i], eps[i], k[i]) pushed together: queries are
- * packed into tiles of 32 or 64 that share every read of the graph, and one
+ * packed into tiles of 32 that share every read of the graph, and one
  * persistent launch runs all tiles.  Host inputs q[n], eps[n], k[n].  Host
  * outputs, concatenated in query order with offsets = exclusive prefix sum of
  * min(k[i], n_u): out_nodes, out_scores; out_n[i] = count for query i.  st
@@ -217,15 +217,19 @@ int ahpp_query_device(ahpp_graph *g, uint32_t q, double eps, uint32_t k,
                       uint32_t *d_out_nodes, float *d_out_scores, uint32_t *d_out_n,
                       ahpp_stats *d_stats, void *stream);
 
-/* Autotune the batched launch shape (tile width x concurrent tiles) by
- * timing a few queries per candidate; the choice is stored in the graph and
- * reported by ahpp_graph_info.  q_sample: host array of n_sample query ids. */
+/* Autotune the batched launch shape (tiles processed concurrently: 1, 2 or
+ * 4) by timing the sample, replicated to fill every candidate; the choice is
+ * stored in the graph and reported by ahpp_get_graph_info.  q_sample: host
+ * array of n_sample query ids (n_sample == 0 changes nothing). */
 int ahpp_autotune(ahpp_graph *g, uint32_t n_sample, const uint32_t *q_sample, double eps);
 
 /* Serving (continuous batching).  A server owns a pool of device slots
- * (one query each) sized by the HBM budget; submitted requests wait in a
- * queue and are admitted into slots as slots free up, while queries already
- * on the device keep advancing one round per step. */
+ * (one query each, in tiles of 32) sized by opts->max_slots or the HBM
+ * budget; submitted requests wait in a queue and are admitted into slots as
+ * slots free up, while queries already on the device keep advancing
+ * rounds_per_step rounds per device step.  Each request may have its own eps
+ * and k.  opts may be NULL (defaults).  AHPP_ENOMEM if not even one tile fits
+ * the budget. */
 int ahpp_server_start(ahpp_graph *g, const ahpp_server_opts *opts, ahpp_server **out);
 
 /* Queue one request; *ticket identifies it.  AHPP_EBUSY if the queue is
