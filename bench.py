@@ -52,6 +52,8 @@ def parse(argv=None):
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--graph", default="medium", choices=["medium", "tiny", "large"])
+    ap.add_argument("--scale", type=float, default=1.0,
+                    help="large graph only: scale |U|, |V|, |E| and |A| by this factor (scalability sweep)")
     ap.add_argument("--ablation", type=int, default=0,
                     help="single-query ablation of the ASRP switch rule and APP on N queries (0: off)")
     ap.add_argument("--serve-seconds", type=float, default=12.0,
@@ -63,21 +65,25 @@ def parse(argv=None):
     return ap.parse_args(argv)
 
 
-def graph_spec(name):
+def graph_spec(name, scale=1.0):
     if name == "large":
-        return dict(synth.LARGE)
+        spec = dict(synth.LARGE)
+        if scale != 1.0:
+            for key in ("n_u", "n_v", "n_e", "n_a"):
+                spec[key] = max(1, int(round(spec[key] * scale)))
+        return spec
     return dict(synth.MEDIUM_BF16) if name == "medium" else dict(synth.TINY, bf16=True)
 
 
 def workload_config(args, extra=None):
-    spec = graph_spec(args.graph)
+    spec = graph_spec(args.graph, args.scale)
     cfg = {
         "workload": (f"{args.graph} attributed bipartite graph |U|={spec['n_u']:,} |V|={spec['n_v']:,} "
                      f"|E|={spec['n_e']:,} Zipf({spec['gamma_u']}) degrees, |A|={spec['n_a']:,} "
                      f"x{spec['m']} bf16 attribute weights; ASRP (Theorem 3 lambda), "
                      f"alpha={ALPHA}, beta={BETA}, eps={args.eps:g}, top-{args.k}; "
                      f"{args.batch} queries per step (batched persistent launch)"),
-        "graph": args.graph,
+        "graph": args.graph if args.scale == 1.0 else f"{args.graph} x{args.scale:g}",
         "batch_queries_per_gpu": args.batch,
         "eps": args.eps,
         "k": args.k,
@@ -238,14 +244,14 @@ def topk_bytes(info, queries):
 
 
 # DRAM bytes (read + write) per tile-round of k_tiles on the medium graph, from
-# the ncu capture summarised in profiles/k_tiles_medium_tile32.md (248.32 GB over
+# the ncu capture summarised in profiles/k_tiles_medium_tile32.md (245.22 GB over
 # the 106 rounds of one 32-query tile).  It describes the kernel built from the
 # sources listed by hash; once any of them changes the figure no longer applies.
 NCU_TRAFFIC = {
     "graph": "medium",
-    "bytes_per_tile_round": 248.32e9 / 106,
-    "sources": {"ahpp_batch.cu": "24d268b83918a951", "ahpp_batch.cuh": "f3dfbbd4287bd668",
-                "ahpp_internal.cuh": "baff201bb1863a8a"},
+    "bytes_per_tile_round": 245.22e9 / 106,
+    "sources": {"ahpp_batch.cu": "b6dcc97015cfcc85", "ahpp_batch.cuh": "f3dfbbd4287bd668",
+                "ahpp_internal.cuh": "64c85a4429923409"},
 }
 
 
@@ -322,7 +328,7 @@ def run_ours(args, rank, world, local_rank):
     import torch
     from paper_2512_11606_gb300 import ahpp
 
-    spec = graph_spec(args.graph)
+    spec = graph_spec(args.graph, args.scale)
     g = synth.make_graph(**spec)
 
     cpu = None
@@ -605,7 +611,7 @@ def run_reference(args, rank, world):
     """The reference arm: the FP64 CPU oracle on the host cores."""
     if rank != 0:
         return None
-    spec = graph_spec(args.graph)
+    spec = graph_spec(args.graph, args.scale)
     g = synth.make_graph(**spec)
     n = args.cpu_queries or min(16, host_cores())
     import oracle
