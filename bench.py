@@ -110,6 +110,14 @@ def _oracle_worker(args):
     return time.perf_counter() - t0, res.stats["rounds"]
 
 
+def _oracle_worker_pi(args):
+    """As _oracle_worker, also returning the reserve vector (for parity)."""
+    q, eps, lam = args
+    t0 = time.perf_counter()
+    res = _OG.push("asrp", ALPHA, BETA, int(q), eps, lam=lam)
+    return time.perf_counter() - t0, res.stats["rounds"], res.pi
+
+
 def cpu_oracle_sample(g, eps, n_queries, seed=11):
     """Time the FP64 oracle (as it stands) on a bounded sample of queries,
     one query per process (fork before any CUDA use)."""
@@ -123,7 +131,7 @@ def cpu_oracle_sample(g, eps, n_queries, seed=11):
     ctx = mp.get_context("fork")
     t1 = time.perf_counter()
     with ctx.Pool(n_queries) as pool:
-        out = pool.map(_oracle_worker, [(int(q), eps, lam) for q in qs])
+        out = pool.map(_oracle_worker_pi, [(int(q), eps, lam) for q in qs])
     wall = time.perf_counter() - t1
     lat = [o[0] for o in out]
     return {
@@ -136,6 +144,8 @@ def cpu_oracle_sample(g, eps, n_queries, seed=11):
                    f"{statistics.median(lat) * 1e3:.0f} ms; oracle lambda {lam:.2f} computed in "
                    f"{prep:.1f} s preprocessing (not timed)"),
         "lambda": lam,
+        "queries": [int(q) for q in qs],
+        "pi": [o[2] for o in out],
         "p50_ms": statistics.median(lat) * 1e3,
         "p99_ms": float(np.percentile(lat, 99)) * 1e3,
     }
@@ -436,6 +446,10 @@ def run_ours(args, rank, world, local_rank):
     if rank == 0 and args.serve_seconds > 0:
         served = run_serving(ahpp, G, g, args, rate=args.serve_load * value / world)
 
+    parity = None
+    if cpu is not None:
+        parity = parity_vs_oracle(G, cpu, args.eps, args.k)
+
     ablation = None
     if rank == 0 and args.ablation > 0:
         ablation = run_ablation(ahpp, g, args, info["lambda"], local_rank)
@@ -486,6 +500,7 @@ def run_ours(args, rank, world, local_rank):
         "not_converged": int((stats["status"] != 0).sum()),
         "mass_err_max": float(stats["mass_err"].max()),
         "roofline": roof,
+        "parity": parity,
         "ablation": ablation,
         "cpu_baseline": cpu and {k: cpu[k] for k in ("value", "unit", "cores", "kind", "sample")},
         "e2e": e2e,
@@ -495,6 +510,28 @@ def run_ours(args, rank, world, local_rank):
     }
     G.close()
     return out
+
+
+def parity_vs_oracle(G, cpu, eps, k):
+    """The oracle's sample queries through the batched GPU path: per query the
+    largest |gpu - oracle| over all of U and the top-k overlap (nodes whose
+    oracle score lies within 2 eps of the k-th count as ties)."""
+    qs = cpu["queries"]
+    dense, _, _ = G.query_batch_dense(qs, eps)
+    res = G.query_batch(qs, eps, k)
+    errs, overlaps = [], []
+    for i, ref in enumerate(cpu["pi"]):
+        errs.append(float(np.abs(dense[i].astype(np.float64) - ref).max()))
+        kk = min(k, ref.shape[0])
+        order = np.lexsort((np.arange(ref.shape[0]), -ref))
+        kth = ref[order[kk - 1]]
+        ok = set(np.nonzero(ref >= kth - 2 * eps)[0].tolist())
+        got = set(res[i].nodes.tolist())
+        overlaps.append(len(got & ok) / kk)
+    return {"queries": len(qs), "eps": eps, "k": k, "bound_abs": 1e-6,
+            "max_abs_err_vs_oracle": max(errs), "per_query_max_abs_err": errs,
+            "topk_overlap_min": min(overlaps), "per_query_topk_overlap": overlaps,
+            "note": "batched GPU results of the CPU-baseline sample vs the FP64 oracle push"}
 
 
 def run_ablation(ahpp, g, args, lam, device):
