@@ -615,6 +615,37 @@ def run_serving(ahpp, G, g, args, rate):
                 "note": "closed loop, requests in flight = slots + a queued backlog; qps over the steady-state window",
             }
 
+        # saturated with the serving workload's request mix: eps log-uniform in
+        # [1e-7, 1e-4], k in {10, 100, 1000} (per-request eps and k in one tile)
+        rng = np.random.default_rng(404)
+        n_mix = n_sat
+        qm = synth.draw_queries(g.n_u, n_mix, seed=405)
+        em = np.exp(rng.uniform(np.log(1e-7), np.log(1e-4), n_mix))
+        km = rng.choice([10, 100, 1000], n_mix)
+        pending = [(srv.submit(int(qm[i]), float(em[i]), int(km[i])), int(km[i])) for i in range(inflight)]
+        nxt = inflight
+        done_t, lat, rounds = [], [], []
+        t0 = time.perf_counter()
+        while pending:
+            t, kk = pending.pop(0)
+            r = srv.wait(t, kk)
+            done_t.append(time.perf_counter() - t0)
+            lat.append(r.stats["served_ms"])
+            rounds.append(r.stats["rounds"])
+            if nxt < n_mix:
+                pending.append((srv.submit(int(qm[nxt]), float(em[nxt]), int(km[nxt])), int(km[nxt])))
+                nxt += 1
+        lo, hi = inflight, n_mix - inflight
+        if hi - lo >= 8:
+            out["saturated_mix"] = {
+                "qps": (hi - lo) / (done_t[hi - 1] - done_t[lo - 1]),
+                "p50_ms": statistics.median(lat[lo:hi]),
+                "p99_ms": float(np.percentile(lat[lo:hi], 99)),
+                "rounds_mean": float(np.mean(rounds)),
+                "queries": n_mix,
+                "note": "closed loop as above; eps log-uniform in [1e-7, 1e-4], k in {10, 100, 1000}",
+            }
+
         # open loop (Poisson arrivals)
         n = max(32, int(rate * args.serve_seconds))
         t_arr, q, _, _ = synth.draw_stream(n, rate, g.n_u, seed=101)

@@ -313,7 +313,10 @@ int build_graph(const ahpp_graph_desc* d, ahpp_graph* g) {
   for (uint32_t v = 0; v < nV; ++v) dg_v[v] = vu_off[v + 1] - vu_off[v];
   for (uint32_t a = 0; a < nA; ++a) dg_a[a] = au_off[a + 1] - au_off[a];
   const ItemShape s1{64, 32, 0xffffffffu, 2048};
-  const uint32_t kUnitChunk = 256;
+#ifndef AHPP_UNIT_CHUNK
+#define AHPP_UNIT_CHUNK 256   // entries per chunk of a long row in the batched pull phases
+#endif
+  const uint32_t kUnitChunk = AHPP_UNIT_CHUNK;
   HostItems i1v = build_items(dg_v, s1), i1a = build_items(dg_a, s1), i1u = build_items(dg_u, s1);
   HostItems ibv = build_units(dg_v, kUnitChunk), iba = build_units(dg_a, kUnitChunk),
             ibu = build_units(dg_u, kUnitChunk);
