@@ -163,3 +163,29 @@ def test_served_latency_is_reported(ahpp, tiny):
         assert r.stats["served_ms"] > 0
     finally:
         srv.stop()
+
+
+def test_served_app_equals_alone_and_oracle(ahpp, tiny):
+    """Serving with APP (Algorithm 3): per-request eps, each served result is
+    the query alone and the oracle's APP push."""
+    g, og = tiny["g"], tiny["og"]
+    G = ahpp.Graph.from_arrays(g, algo=ahpp.AHPP_APP, attr_bf16=0)
+    try:
+        qs = synth.draw_queries(g.n_u, 40, seed=81)
+        eps = [1e-6 if i % 2 else 1e-4 for i in range(40)]
+        srv = ahpp.Server(G, max_slots=32, rounds_per_step=3)
+        try:
+            t = [srv.submit(int(q), e, 50) for q, e in zip(qs, eps)]
+            res = [srv.wait(x, 50) for x in t]
+        finally:
+            srv.stop()
+        for i in [0, 1, 31, 32, 39]:
+            r = res[i]
+            assert r.rc == 0 and r.stats["status"] == 0
+            alone = G.query(int(qs[i]), eps[i], 50)
+            check_same(r, alone, 50)
+            assert r.stats["rounds"] == alone.stats["rounds"]
+            ref = og.push("app", ALPHA, BETA, int(qs[i]), eps[i])
+            assert np.all(np.abs(r.scores - ref.pi[r.nodes]) <= max(TOL, eps[i]))
+    finally:
+        G.close()
