@@ -10,8 +10,9 @@ Large (|U|=|V|=5M, |E|=200M, |A|=50k x 30, 256-query batch, top-1,000):
 too big for the oracle's exact push in a test, so it is checked through
 properties that hold at any size: mass conservation, nonnegativity, the
 batched result equal to the result alone, and top-k consistent with the
-reserves.  Generating that graph takes minutes on the host, so the test runs
-only with AHPP_LARGE=1.
+reserves; Theorem 2 against the GPU's Algorithm 1; and serving with the
+serving workload's request mix.  Generating that graph takes minutes on the
+host, so the test runs only with AHPP_LARGE=1.
 """
 import os
 
@@ -101,6 +102,24 @@ def test_medium_single_and_batched_vs_oracle(medium):
         assert dense[i][r.nodes].min() >= kth_i - 2 * TOL
 
 
+@pytest.mark.parametrize("eps", [1e-5, 1e-7])
+def test_medium_single_query_other_eps(medium, eps):
+    """The single-query workload's other error thresholds: every score within
+    1e-6 of the oracle push, top-100 overlap with the oracle >= 0.99."""
+    G, og, lam, g = medium["G"], medium["og"], medium["lam"], medium["g"]
+    q = int(synth.draw_queries(g.n_u, 2, seed=7)[1])
+    ref = og.push("asrp", ALPHA, BETA, q, eps, lam=lam)
+    pi, st, rc = G.query_dense(q, eps)
+    assert rc == 0 and st["status"] == 0
+    assert np.abs(pi.astype(np.float64) - ref.pi).max() <= max(TOL, eps)
+    assert abs(st["rounds"] - ref.stats["rounds"]) <= 1
+    top = G.query(q, eps, 100)
+    order = np.lexsort((np.arange(g.n_u), -ref.pi))
+    kth = ref.pi[order[99]]
+    ok = set(np.nonzero(ref.pi >= kth - 2 * max(eps, TOL))[0].tolist())
+    assert len(set(top.nodes.tolist()) & ok) / 100 >= 0.99
+
+
 def test_medium_served_mix_equals_alone(ahpp, medium):
     """Continuous batching at full size with the serving workload's request
     mix (eps log-uniform in [1e-7, 1e-4], k in {10, 100, 1000}): requests
@@ -162,5 +181,23 @@ def test_large_graph_properties(ahpp):
         assert rc == 0
         d = pi_T.astype(np.float64) - alone.astype(np.float64)
         assert d.min() >= -5e-7 and d.max() <= eps + 5e-7
+        # serving on the large graph with the serving workload's request mix
+        rng = np.random.default_rng(23)
+        ns = 40
+        sq = synth.draw_queries(g.n_u, ns, seed=29)
+        se = np.exp(rng.uniform(np.log(1e-7), np.log(1e-4), ns))
+        sk = rng.choice([10, 100, 1000], ns)
+        srv = ahpp.Server(G, max_slots=32, rounds_per_step=8)
+        try:
+            tk = [srv.submit(int(sq[i]), float(se[i]), int(sk[i])) for i in range(ns)]
+            sr = [srv.wait(t, int(k)) for t, k in zip(tk, sk)]
+        finally:
+            srv.stop()
+        for i in (0, 17, 33, 39):
+            assert sr[i].rc == 0 and sr[i].stats["mass_err"] < 1e-5
+            one = G.query(int(sq[i]), float(se[i]), int(sk[i]))
+            assert sr[i].stats["rounds"] == one.stats["rounds"]
+            common = len(set(sr[i].nodes.tolist()) & set(one.nodes.tolist())) / int(sk[i])
+            assert common >= 0.98
     finally:
         G.close()
