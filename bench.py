@@ -646,6 +646,25 @@ def run_serving(ahpp, G, g, args, rate):
                 "note": "closed loop as above; eps log-uniform in [1e-7, 1e-4], k in {10, 100, 1000}",
             }
 
+        # light load: Poisson arrivals at 5 % of the batched capacity; the server
+        # answers most requests on the single-query path
+        rate_l = 0.05 * rate / max(args.serve_load, 1e-3)
+        n_l = max(16, int(rate_l * min(6.0, args.serve_seconds)))
+        t_arr, ql, _, _ = synth.draw_stream(n_l, rate_l, g.n_u, seed=103)
+        tickets = []
+        t0 = time.perf_counter()
+        for i in range(n_l):
+            delay = t0 + t_arr[i] - time.perf_counter()
+            if delay > 0:
+                time.sleep(delay)
+            tickets.append(srv.submit(int(ql[i]), args.eps, args.k))
+        lat = [srv.wait(t, args.k).stats["served_ms"] for t in tickets]
+        out["open_loop_light"] = {
+            "rate_qps": rate_l, "queries": n_l, "p50_ms": statistics.median(lat),
+            "p99_ms": float(np.percentile(lat, 99)),
+            "note": "Poisson arrivals at 5 % of the batched capacity (single-query path at light load)",
+        }
+
         # open loop (Poisson arrivals)
         n = max(32, int(rate * args.serve_seconds))
         t_arr, q, _, _ = synth.draw_stream(n, rate, g.n_u, seed=101)

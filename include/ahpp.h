@@ -121,6 +121,10 @@ typedef struct {
     uint32_t queue_capacity;   /* pending requests before AHPP_EBUSY; 0: 65536 */
     uint32_t tile;             /* queries per tile; 0 or the library's tile width */
     uint32_t rounds_per_step;  /* push rounds per device step between admissions; 0: 4 */
+    int32_t single_max;        /* light load: while no tile lane runs and at most this many
+                                  requests wait, answer the oldest on the single-query path
+                                  (lower latency than a tile round for one query);
+                                  0: 3, < 0: never */
 } ahpp_server_opts;
 
 /* Fill *cfg with the defaults listed above. */

@@ -70,7 +70,8 @@ class GraphInfo(ctypes.Structure):
 
 class ServerOpts(ctypes.Structure):
     _fields_ = [("max_slots", ctypes.c_uint32), ("queue_capacity", ctypes.c_uint32),
-                ("tile", ctypes.c_uint32), ("rounds_per_step", ctypes.c_uint32)]
+                ("tile", ctypes.c_uint32), ("rounds_per_step", ctypes.c_uint32),
+                ("single_max", ctypes.c_int32)]
 
 
 class ServerInfo(ctypes.Structure):
@@ -322,9 +323,9 @@ class Server:
     """Continuous-batching server over a loaded graph."""
 
     def __init__(self, graph: Graph, max_slots: int = 0, queue_capacity: int = 0, tile: int = 0,
-                 rounds_per_step: int = 0):
+                 rounds_per_step: int = 0, single_max: int = 0):
         self.graph = graph
-        o = ServerOpts(max_slots, queue_capacity, tile, rounds_per_step)
+        o = ServerOpts(max_slots, queue_capacity, tile, rounds_per_step, single_max)
         h = _vp()
         _check(lib().ahpp_server_start(graph.handle, ctypes.byref(o), ctypes.byref(h)))
         self._h = h

@@ -233,6 +233,25 @@ int run_batch_launch(ahpp_graph* g, uint32_t n, const uint32_t* d_q, const doubl
   return AHPP_OK;
 }
 
+// The plain path into device buffers, on `s`; the caller holds g->mu and has
+// validated the arguments.
+int run_single_device(ahpp_graph* g, uint32_t q, double eps, uint32_t k, uint32_t* d_out_nodes,
+                      float* d_out_scores, uint32_t* d_out_n, ahpp_stats* d_stats, cudaStream_t s) {
+  int rc = run_query1_launch(g, g->h_u_old2new[q], eps, s);
+  if (rc) return rc;
+  if (k) {
+    rc = topk_single(g, g->q1.pi, k, d_out_nodes, d_out_scores, d_out_n, s);
+    if (rc) return rc;
+  } else if (d_out_n) {
+    AHPP_CUDA(cudaMemsetAsync(d_out_n, 0, 4, s));
+  }
+  if (d_stats) {
+    k_ctl_to_stats<<<1, 1, 0, s>>>(g->q1.ctl, g->q1.final_maxr_bits, g->lambda, eps_f_of(g, eps), d_stats);
+    AHPP_CUDA(cudaGetLastError());
+  }
+  return AHPP_OK;
+}
+
 }  // namespace ahpp
 
 using namespace ahpp;
@@ -381,6 +400,7 @@ int ahpp_get_graph_info(const ahpp_graph* g, ahpp_graph_info* info) {
   return AHPP_OK;
 }
 
+
 int ahpp_query_device(ahpp_graph* g, uint32_t q, double eps, uint32_t k, uint32_t* d_out_nodes,
                       float* d_out_scores, uint32_t* d_out_n, ahpp_stats* d_stats, void* stream) {
   if (!g) { set_error("null graph"); return AHPP_EINVAL; }
@@ -391,17 +411,7 @@ int ahpp_query_device(ahpp_graph* g, uint32_t q, double eps, uint32_t k, uint32_
   std::lock_guard<std::mutex> lock(g->mu);
   AHPP_CUDA(cudaSetDevice(g->device));
   cudaStream_t s = stream ? (cudaStream_t)stream : g->stream;
-  int rc = run_query1_launch(g, g->h_u_old2new[q], eps, s);
-  if (rc) return rc;
-  if (k) {
-    rc = topk_single(g, g->q1.pi, k, d_out_nodes, d_out_scores, d_out_n, s);
-    if (rc) return rc;
-  }
-  if (d_stats) {
-    k_ctl_to_stats<<<1, 1, 0, s>>>(g->q1.ctl, g->q1.final_maxr_bits, g->lambda, eps_f_of(g, eps), d_stats);
-    AHPP_CUDA(cudaGetLastError());
-  }
-  return AHPP_OK;
+  return ahpp::run_single_device(g, q, eps, k, d_out_nodes, d_out_scores, d_out_n, d_stats, s);
 }
 
 static int finish_single(ahpp_graph* g, double eps, ahpp_stats* st) {

@@ -106,4 +106,6 @@ int run_query1(ahpp_graph* g, uint32_t q_new, double eps, uint32_t lambda_T_mode
                cudaStream_t stream, QCtl* h_ctl);
 int topk_single(ahpp_graph* g, const float* d_score, uint32_t k, uint32_t* d_nodes,
                 float* d_scores, uint32_t* d_n, cudaStream_t stream);
+int run_single_device(ahpp_graph* g, uint32_t q, double eps, uint32_t k, uint32_t* d_out_nodes,
+                      float* d_out_scores, uint32_t* d_out_n, ahpp_stats* d_stats, cudaStream_t s);
 }  // namespace ahpp

@@ -52,6 +52,7 @@ struct Result {
 struct ahpp_server {
   ahpp_graph* g = nullptr;
   uint32_t n_tiles = 0, n_slots = 0, kmax = AHPP_MAX_K, queue_cap = 65536, rounds_per_step = 4;
+  int32_t single_max = 3;
   int grid = 0;
   cudaStream_t stream = nullptr;
   std::vector<void*> allocs;
@@ -98,8 +99,57 @@ struct ahpp_server {
 
 namespace {
 
+// Light load: one request on the single-query path (the whole GPU on one
+// query), its results through slot 0's output buffers (no tile lane runs).
+int single_step(ahpp_server* s, const Request& r) {
+  ahpp_graph* g = s->g;
+  Result res;
+  const uint32_t kk = (uint32_t)std::min<uint64_t>(r.k, g->n_u);
+  res.nodes.resize(kk);
+  res.scores.resize(kk);
+  {
+    std::lock_guard<std::mutex> glock(g->mu);
+    int rc = run_single_device(g, r.q, r.eps, kk, s->d_nodes, s->d_scores, s->d_n, s->d_stats, s->stream);
+    if (rc) return rc;
+    if (kk) {
+      AHPP_CUDA(cudaMemcpyAsync(res.nodes.data(), s->d_nodes, 4ull * kk, cudaMemcpyDeviceToHost, s->stream));
+      AHPP_CUDA(cudaMemcpyAsync(res.scores.data(), s->d_scores, 4ull * kk, cudaMemcpyDeviceToHost, s->stream));
+    }
+    AHPP_CUDA(cudaMemcpyAsync(&res.st, s->d_stats, sizeof(ahpp_stats), cudaMemcpyDeviceToHost, s->stream));
+    AHPP_CUDA(cudaStreamSynchronize(s->stream));
+  }
+  const Clock::time_point now = Clock::now();
+  res.st.served_ms = std::chrono::duration<double, std::milli>(now - r.t_submit).count();
+  res.rc = res.st.status == kStatusCap ? AHPP_ENOTCONVERGED : res.st.status == kStatusWait ? AHPP_ETIMEOUT : AHPP_OK;
+  {
+    std::lock_guard<std::mutex> lock(s->mu);
+    s->done[r.ticket] = std::move(res);
+    --s->in_flight;
+    ++s->completed;
+    ++s->steps;
+  }
+  s->cv_done.notify_all();
+  return AHPP_OK;
+}
+
 int server_step(ahpp_server* s) {
   ahpp_graph* g = s->g;
+  // 0. light load: nothing in the tiles and a short queue
+  {
+    Request r{};
+    bool single = false;
+    {
+      std::lock_guard<std::mutex> lock(s->mu);
+      if (s->single_max > 0 && s->in_flight == 0 && !s->queue.empty() &&
+          s->queue.size() <= (size_t)s->single_max) {
+        r = s->queue.front();
+        s->queue.pop_front();
+        ++s->in_flight;
+        single = true;
+      }
+    }
+    if (single) return single_step(s, r);
+  }
   // 1. admission (under the lock)
   std::vector<uint32_t> live;
   {
@@ -236,6 +286,7 @@ int ahpp_server_start(ahpp_graph* g, const ahpp_server_opts* opts, ahpp_server**
   s->g = g;
   if (o.queue_capacity) s->queue_cap = o.queue_capacity;
   if (o.rounds_per_step) s->rounds_per_step = o.rounds_per_step;
+  if (o.single_max) s->single_max = o.single_max;
   // slots: requested, else what the HBM budget leaves after the graph, else 8 tiles
   const DevGraph& G = g->dg;
   const size_t n_split = std::max((size_t)G.b_v.n_split + G.b_a.n_split + G.b_u.n_split,

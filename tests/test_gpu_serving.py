@@ -189,3 +189,28 @@ def test_served_app_equals_alone_and_oracle(ahpp, tiny):
             assert np.all(np.abs(r.scores - ref.pi[r.nodes]) <= max(TOL, eps[i]))
     finally:
         G.close()
+
+
+def test_light_load_uses_the_single_query_path(ahpp, tiny):
+    """With nothing running and a short queue the server answers on the
+    single-query path (the plain query's kernel, equal up to the order of its
+    FP32 atomic sums).  With the single path disabled the same request goes
+    through a tile and matches within the tolerance."""
+    G = tiny["G"]
+    q, eps, k = 17, 1e-6, 20
+    alone = G.query(q, eps, k)
+    srv = ahpp.Server(G, max_slots=32)
+    try:
+        r = srv.wait(srv.submit(q, eps, k), k)
+    finally:
+        srv.stop()
+    check_same(r, alone, k)
+    assert r.stats["rounds"] == alone.stats["rounds"] and r.stats["served_ms"] > 0
+    assert r.stats["dense_rounds"] == alone.stats["dense_rounds"]   # the plain path's push/pull split
+    srv = ahpp.Server(G, max_slots=32, single_max=-1)
+    try:
+        r2 = srv.wait(srv.submit(q, eps, k), k)
+    finally:
+        srv.stop()
+    check_same(r2, alone, k)
+    assert r2.stats["rounds"] == alone.stats["rounds"]
