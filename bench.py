@@ -593,6 +593,8 @@ def run_serving(ahpp, G, g, args, rate):
         n_sat = max(4 * slots, int(args.serve_seconds * rate / max(args.serve_load, 1e-3) / 2))
         inflight = slots + max(4, slots // 4)
         qs = synth.draw_queries(g.n_u, n_sat, seed=202)
+        clk = ClockSampler(gpu_index(G.info["device"]))
+        clk.start()
         pending = [srv.submit(int(q), args.eps, args.k) for q in qs[:inflight]]
         nxt = inflight
         done_t, lat = [], []
@@ -604,6 +606,7 @@ def run_serving(ahpp, G, g, args, rate):
             if nxt < n_sat:
                 pending.append(srv.submit(int(qs[nxt]), args.eps, args.k))
                 nxt += 1
+        sat_clocks = clk.stop()
         lo, hi = inflight, n_sat - inflight    # steady state: after the first wave, before the drain
         if hi - lo >= 8:
             out["saturated"] = {
@@ -612,6 +615,7 @@ def run_serving(ahpp, G, g, args, rate):
                 "p99_ms": float(np.percentile(lat[lo:hi], 99)),
                 "queries": n_sat, "window_queries": hi - lo,
                 "in_flight": inflight,
+                "clocks": sat_clocks,
                 "note": "closed loop, requests in flight = slots + a queued backlog; qps over the steady-state window",
             }
 
