@@ -260,14 +260,16 @@ def topk_bytes(info, queries):
 NCU_TRAFFIC = {
     "graph": "medium",
     "bytes_per_tile_round": 245.22e9 / 106,
+    # l1tex__m_xbar2l1tex_read_bytes.sum of the same capture: bytes moved from L2 to the SMs
+    "l2_to_sm_bytes_per_tile_round": 1.257278e12 / 106,
     "sources": {"ahpp_batch.cu": "b6dcc97015cfcc85", "ahpp_batch.cuh": "f3dfbbd4287bd668",
                 "ahpp_internal.cuh": "64c85a4429923409"},
 }
 
 
-def ncu_traffic(graph, tile_rounds):
-    """DRAM bytes of one launch scaled from the capture, or None if it does
-    not describe the kernel as built now."""
+def ncu_traffic(graph, tile_rounds, key="bytes_per_tile_round"):
+    """Bytes of one launch scaled from the capture (DRAM by default, or the
+    L2 -> SM bytes), or None if it does not describe the kernel as built now."""
     import hashlib
     if graph != NCU_TRAFFIC["graph"]:
         return None
@@ -276,7 +278,7 @@ def ncu_traffic(graph, tile_rounds):
         with open(os.path.join(csrc, name), "rb") as f:
             if hashlib.sha256(f.read()).hexdigest()[:16] != want:
                 return None
-    return NCU_TRAFFIC["bytes_per_tile_round"] * tile_rounds
+    return NCU_TRAFFIC[key] * tile_rounds
 
 
 def row_roofline(ahpp, info, tile_rounds, launch_s, device):
@@ -471,6 +473,18 @@ def run_ours(args, rank, world, local_rank):
         roof["l2_rows"] = row_roofline(ahpp, info, tile_rounds, sum(launch_ms) / K / 1e3, local_rank)
     except Exception as e:  # the HBM roofline above stands on its own
         roof["l2_rows"] = {"error": str(e)}
+    # L2 -> SM bytes (ncu capture, scaled) against the measured rate of random
+    # 128-byte row gathers from an L2-resident table of the t_V size
+    l2_bytes = ncu_traffic(args.graph, tile_rounds, "l2_to_sm_bytes_per_tile_round")
+    parts = roof["l2_rows"].get("parts") if isinstance(roof.get("l2_rows"), dict) else None
+    if l2_bytes and parts:
+        peak_l2 = parts[1]["peak_rows_per_s"] * 4 * int(info["batch_tile"]) / 1e9
+        ach_l2 = l2_bytes / (sum(launch_ms) / K / 1e3) / 1e9
+        roof["l2_sm"] = {"bound": "l2 -> sm bandwidth", "unit": "GB/s", "achieved": ach_l2, "peak": peak_l2,
+                         "frac": ach_l2 / peak_l2,
+                         "note": ("achieved = ncu l1tex__m_xbar2l1tex_read_bytes per tile-round x tile-rounds / "
+                                  "launch time; peak = measured random 128-byte row gathers from an "
+                                  "L2-resident table (byte-limited: 64-512 B rows reach the same GB/s)")}
 
     lat_ms = launch_ms
     out = {
