@@ -271,6 +271,16 @@ int ahpp_server_stop(ahpp_server *s);
  * AHPP_ENOMEM if the table cannot be allocated; AHPP_ECUDA otherwise. */
 int ahpp_row_access_peak(int device, uint64_t table_bytes, int op, double *rows_per_s);
 
+/* Self-test of the device-side failure detection (no graph needed).  Every
+ * wait inside the persistent kernels is a grid barrier whose spin is bounded
+ * (about a second); when it gives up it raises an error flag, the kernel
+ * unwinds and the query reports AHPP_ETIMEOUT.  This runs that barrier with
+ * more participants than blocks, so it can never fill: *blocks_gave_up
+ * receives how many blocks reported giving up (2 expected) and *context_ok
+ * whether a kernel launched afterwards ran (1 expected).  Takes a few
+ * seconds.  AHPP_EINVAL for bad arguments, AHPP_ECUDA if a CUDA call fails. */
+int ahpp_selftest_wait_timeout(int device, int *blocks_gave_up, int *context_ok);
+
 #ifdef __cplusplus
 }
 #endif

@@ -114,6 +114,8 @@ SIGNATURES = {
                                             ctypes.POINTER(Stats)]),
     "ahpp_row_access_peak": (ctypes.c_int, [ctypes.c_int, ctypes.c_uint64, ctypes.c_int,
                                             ctypes.POINTER(ctypes.c_double)]),
+    "ahpp_selftest_wait_timeout": (ctypes.c_int, [ctypes.c_int, ctypes.POINTER(ctypes.c_int),
+                                                  ctypes.POINTER(ctypes.c_int)]),
 }
 
 
@@ -308,6 +310,13 @@ class Graph:
 
 
 STATS_BYTES = ctypes.sizeof(Stats)
+
+
+def selftest_wait_timeout(device: int = 0):
+    """(blocks that reported a given-up device wait, context usable after)."""
+    a, b = ctypes.c_int(0), ctypes.c_int(0)
+    _check(lib().ahpp_selftest_wait_timeout(device, ctypes.byref(a), ctypes.byref(b)))
+    return a.value, bool(b.value)
 
 
 def row_access_peak(table_bytes: int, op: str = "gather", device: int = 0) -> float:

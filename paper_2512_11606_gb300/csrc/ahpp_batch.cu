@@ -1218,8 +1218,10 @@ const void* tiles_fn(bool bf16, bool serve) {
 }  // namespace
 
 // Tensor maps of a tile buffer for the TMA row gathers: r_U ([n_u][kTile]),
-// t_V ([n_v][kTile]) and t_A ([n_a][kTile]); box kTile x 1.
+// t_V ([n_v][kTile]) and t_A ([n_a][kTile]); box kTile x 1.  Only the TMA
+// phases read them, so a build without them encodes nothing.
 int encode_tile_maps(TileBuf& t, uint32_t n_u, uint32_t n_v, uint32_t n_a) {
+  if (!AHPP_TMA) return 0;
   typedef CUresult (*EncodeFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
                                const cuuint64_t*, const cuuint32_t*, const cuuint32_t*,
                                CUtensorMapInterleave, CUtensorMapSwizzle, CUtensorMapL2promotion,

@@ -1,8 +1,9 @@
 """The remaining public paths of the C ABI against the host paths and the oracle.
 
 Device-resident calls (the launch bench.py times), the ASRP switch rules,
-concurrent tile groups and the autotuner, APP in the batched kernel, and the
-batch edge cases (empty batch, k clamped to |U|).
+concurrent tile groups and the autotuner, APP in the batched kernel, the
+batch edge cases (empty batch, k clamped to |U|), and the device-side
+failure detection (a bounded wait that gives up and reports it).
 """
 import ctypes
 
@@ -180,3 +181,13 @@ def test_empty_batch_and_k_clamped(ahpp, tiny):
     with pytest.raises(ahpp.AhppError) as e:
         G.query_batch([3], 1e-6, ahpp.AHPP_MAX_K + 1)
     assert e.value.code == ahpp.AHPP_EINVAL
+
+
+def test_device_wait_gives_up_and_context_survives(ahpp, tiny):
+    """Failure detection without a fault: a grid barrier that can never fill
+    gives up within its bounded spin, reports it, and the context keeps
+    working (a query runs afterwards)."""
+    gave_up, ctx_ok = ahpp.selftest_wait_timeout(0)
+    assert gave_up == 2 and ctx_ok
+    r = tiny["G"].query(3, 1e-4, 5)
+    assert r.rc == 0 and r.nodes.shape[0] == 5
