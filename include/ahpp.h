@@ -44,6 +44,7 @@ extern "C" {
 #define AHPP_EBUSY (-5)           /* serving: no free slot / admission queue full */
 #define AHPP_ETIMEOUT (-6)        /* serving: wait timed out, or a device wait gave up */
 #define AHPP_ESTATE (-7)          /* handle used in the wrong state (e.g. server stopped) */
+#define AHPP_ECANCELED (-8)       /* serving: the request was cancelled (ahpp_cancel) */
 
 #define AHPP_APP 1                /* Algorithm 3 */
 #define AHPP_ASRP 2               /* Algorithm 4 */
@@ -247,6 +248,14 @@ int ahpp_submit(ahpp_server *s, uint32_t q, double eps, uint32_t k, uint64_t *ti
  * delivered once. */
 int ahpp_wait(ahpp_server *s, uint64_t ticket, int timeout_ms, uint32_t *nodes, float *scores,
               uint32_t *n, ahpp_stats *st);
+
+/* Cancel a submitted request that has not been delivered.  A queued request
+ * is dropped; a request already on the device gives up its slot at the next
+ * step boundary.  Its ahpp_wait then returns AHPP_ECANCELED, unless the
+ * query finished before the cancellation took effect, in which case the
+ * result is delivered as usual.  AHPP_EINVAL for an unknown or already
+ * delivered ticket. */
+int ahpp_cancel(ahpp_server *s, uint64_t ticket);
 
 /* Server counters: completed, in flight, queued, rejected, device steps. */
 typedef struct {

@@ -17,6 +17,7 @@ LIB_PATH = os.environ.get("AHPP_LIB") or os.path.join(HERE, "_build", "libahpp_g
 
 AHPP_OK, AHPP_EINVAL, AHPP_ENOMEM, AHPP_ECUDA = 0, -1, -2, -3
 AHPP_ENOTCONVERGED, AHPP_EBUSY, AHPP_ETIMEOUT, AHPP_ESTATE = -4, -5, -6, -7
+AHPP_ECANCELED = -8
 AHPP_APP, AHPP_ASRP = 1, 2
 AHPP_MAX_K = 4096
 
@@ -110,6 +111,7 @@ SIGNATURES = {
                                  ctypes.POINTER(Stats)]),
     "ahpp_server_info_get": (ctypes.c_int, [_vp, ctypes.POINTER(ServerInfo)]),
     "ahpp_server_stop": (ctypes.c_int, [_vp]),
+    "ahpp_cancel": (ctypes.c_int, [_vp, ctypes.c_uint64]),
     "ahpp_power_iteration": (ctypes.c_int, [_vp, ctypes.c_uint32, ctypes.c_uint32, _f32p,
                                             ctypes.POINTER(Stats)]),
     "ahpp_row_access_peak": (ctypes.c_int, [ctypes.c_int, ctypes.c_uint64, ctypes.c_int,
@@ -361,8 +363,13 @@ class Server:
                              ctypes.byref(n), ctypes.byref(st))
         if rc == AHPP_ETIMEOUT:
             return None
-        _check(rc, (AHPP_ENOTCONVERGED,))
+        _check(rc, (AHPP_ENOTCONVERGED, AHPP_ECANCELED))
         return QueryResult(nodes[: n.value], scores[: n.value], st.as_dict(), rc)
+
+    def cancel(self, ticket: int) -> int:
+        """Drop a queued request or free its slot at the next step; its wait
+        then returns rc AHPP_ECANCELED (unless it finished first)."""
+        return _check(lib().ahpp_cancel(self._h, ticket))
 
     def info(self) -> dict:
         i = ServerInfo()

@@ -324,6 +324,7 @@ void ahpp_config_default(ahpp_config* c) {
 const char* ahpp_last_error(void) { return t_err.c_str(); }
 
 int ahpp_load_graph(const ahpp_graph_desc* desc, const ahpp_config* cfg, ahpp_graph** out) {
+  ahpp::NvtxRange nvtx_range_("ahpp_load_graph");
   if (!desc || !out) { set_error("ahpp_load_graph: null argument"); return AHPP_EINVAL; }
   *out = nullptr;
   ahpp_config c;
@@ -403,6 +404,7 @@ int ahpp_get_graph_info(const ahpp_graph* g, ahpp_graph_info* info) {
 
 int ahpp_query_device(ahpp_graph* g, uint32_t q, double eps, uint32_t k, uint32_t* d_out_nodes,
                       float* d_out_scores, uint32_t* d_out_n, ahpp_stats* d_stats, void* stream) {
+  ahpp::NvtxRange nvtx_range_("ahpp_query_device");
   if (!g) { set_error("null graph"); return AHPP_EINVAL; }
   if (q >= g->n_u) { set_error("q is not a node of U"); return AHPP_EINVAL; }
   if (int rc = check_eps(eps)) return rc;
@@ -441,6 +443,7 @@ static int finish_single(ahpp_graph* g, double eps, ahpp_stats* st) {
 }
 
 int ahpp_power_iteration(ahpp_graph* g, uint32_t q, uint32_t T, float* out_pi, ahpp_stats* st) {
+  ahpp::NvtxRange nvtx_range_("ahpp_power_iteration");
   if (!g || !out_pi) { set_error("null argument"); return AHPP_EINVAL; }
   if (q >= g->n_u) { set_error("q is not a node of U"); return AHPP_EINVAL; }
   if (T == 0 || T > kMaxPowerIterations) {
@@ -474,6 +477,7 @@ int ahpp_power_iteration(ahpp_graph* g, uint32_t q, uint32_t T, float* out_pi, a
 
 int ahpp_query(ahpp_graph* g, uint32_t q, double eps, uint32_t k, uint32_t* out_nodes,
                float* out_scores, uint32_t* out_n, ahpp_stats* st) {
+  ahpp::NvtxRange nvtx_range_("ahpp_query");
   if (!g) { set_error("null graph"); return AHPP_EINVAL; }
   if (q >= g->n_u) { set_error("q is not a node of U"); return AHPP_EINVAL; }
   if (int rc = check_eps(eps)) return rc;
@@ -500,6 +504,7 @@ int ahpp_query(ahpp_graph* g, uint32_t q, double eps, uint32_t k, uint32_t* out_
 }
 
 int ahpp_query_dense(ahpp_graph* g, uint32_t q, double eps, float* out_pi, ahpp_stats* st) {
+  ahpp::NvtxRange nvtx_range_("ahpp_query_dense");
   if (!g || !out_pi) { set_error("null argument"); return AHPP_EINVAL; }
   if (q >= g->n_u) { set_error("q is not a node of U"); return AHPP_EINVAL; }
   if (int rc = check_eps(eps)) return rc;
@@ -520,6 +525,7 @@ int ahpp_query_batch_device(ahpp_graph* g, uint32_t n, const uint32_t* d_q, cons
                             const uint32_t* d_k, uint32_t kmax, uint32_t* d_out_nodes,
                             float* d_out_scores, uint32_t* d_out_n, ahpp_stats* d_stats,
                             void* stream) {
+  ahpp::NvtxRange nvtx_range_("ahpp_query_batch_device");
   if (!g) { set_error("null graph"); return AHPP_EINVAL; }
   if (n == 0) return AHPP_OK;
   if (!d_q || !d_eps) { set_error("null input"); return AHPP_EINVAL; }
@@ -605,11 +611,13 @@ static int batch_host(ahpp_graph* g, uint32_t n, const uint32_t* q, const double
 int ahpp_query_batch(ahpp_graph* g, uint32_t n, const uint32_t* q, const double* eps,
                      const uint32_t* k, uint32_t* out_nodes, float* out_scores, uint32_t* out_n,
                      ahpp_stats* st) {
+  ahpp::NvtxRange nvtx_range_("ahpp_query_batch");
   return batch_host(g, n, q, eps, k, out_nodes, out_scores, out_n, st, nullptr);
 }
 
 int ahpp_query_batch_dense(ahpp_graph* g, uint32_t n, const uint32_t* q, const double* eps,
                            float* out_pi, ahpp_stats* st) {
+  ahpp::NvtxRange nvtx_range_("ahpp_query_batch_dense");
   if (!out_pi) { set_error("null output"); return AHPP_EINVAL; }
   return batch_host(g, n, q, eps, nullptr, nullptr, nullptr, nullptr, st, out_pi);
 }

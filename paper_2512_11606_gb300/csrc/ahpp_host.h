@@ -8,12 +8,23 @@
 #include <string>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "../../include/ahpp.h"
 #include "ahpp_internal.cuh"
 #include "ahpp_query1.cuh"
 #include "ahpp_batch.cuh"
 
 namespace ahpp {
+
+// NVTX range over a host call (visible in a profiler's timeline; the calls
+// do nothing unless a tool is attached).
+struct NvtxRange {
+  explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+  ~NvtxRange() { nvtxRangePop(); }
+  NvtxRange(const NvtxRange&) = delete;
+  NvtxRange& operator=(const NvtxRange&) = delete;
+};
 
 void set_error(const std::string& msg);
 int cuda_fail(cudaError_t e, const char* where);

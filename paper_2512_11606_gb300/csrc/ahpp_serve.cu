@@ -74,6 +74,7 @@ struct ahpp_server {
   std::condition_variable cv_work, cv_done;
   std::deque<Request> queue;
   std::unordered_set<uint64_t> pending;
+  std::unordered_set<uint64_t> cancel_req;   // in-flight tickets to drop at the next step
   std::unordered_map<uint64_t, Result> done;
   uint64_t next_ticket = 1, submitted = 0, completed = 0, rejected = 0, steps = 0;
   uint32_t in_flight = 0;
@@ -132,8 +133,35 @@ int single_step(ahpp_server* s, const Request& r) {
   return AHPP_OK;
 }
 
+// Cancelled in-flight requests give up their slots (under s->mu, between
+// steps: the device holds no step of this server at this point).
+void apply_cancellations(ahpp_server* s) {
+  if (s->cancel_req.empty()) return;
+  bool any = false;
+  for (uint32_t slot = 0; slot < s->n_slots; ++slot) {
+    SlotState& S = s->h_slots[slot];
+    if (S.state != kSlotNew && S.state != kSlotRunning) continue;
+    const uint64_t t = s->slot_ticket[slot];
+    if (!s->cancel_req.count(t)) continue;
+    S.state = kSlotFree;
+    Result r;
+    r.rc = AHPP_ECANCELED;
+    s->done[t] = std::move(r);
+    s->cancel_req.erase(t);
+    --s->in_flight;
+    any = true;
+  }
+  s->cancel_req.clear();      // the rest finished before the cancellation took effect
+  if (any) s->cv_done.notify_all();
+}
+
 int server_step(ahpp_server* s) {
+  NvtxRange nvtx_range_("ahpp_server_step");
   ahpp_graph* g = s->g;
+  {
+    std::lock_guard<std::mutex> lock(s->mu);
+    apply_cancellations(s);
+  }
   // 0. light load: nothing in the tiles and a short queue
   {
     Request r{};
@@ -425,6 +453,30 @@ int ahpp_wait(ahpp_server* s, uint64_t ticket, int timeout_ms, uint32_t* nodes, 
   if (n) *n = (uint32_t)r.nodes.size();
   if (st) *st = r.st;
   return r.rc;
+}
+
+int ahpp_cancel(ahpp_server* s, uint64_t ticket) {
+  if (!s) { set_error("ahpp_cancel: null server"); return AHPP_EINVAL; }
+  {
+    std::lock_guard<std::mutex> lock(s->mu);
+    if (!s->pending.count(ticket)) {
+      set_error("ahpp_cancel: unknown or already delivered ticket");
+      return AHPP_EINVAL;
+    }
+    if (s->done.count(ticket)) return AHPP_OK;      // finished: its result is delivered as usual
+    for (auto it = s->queue.begin(); it != s->queue.end(); ++it) {
+      if (it->ticket != ticket) continue;
+      s->queue.erase(it);
+      Result r;
+      r.rc = AHPP_ECANCELED;
+      s->done[ticket] = std::move(r);
+      s->cv_done.notify_all();
+      return AHPP_OK;
+    }
+    s->cancel_req.insert(ticket);      // on the device: dropped at the next step
+  }
+  s->cv_work.notify_one();
+  return AHPP_OK;
 }
 
 int ahpp_server_info_get(ahpp_server* s, ahpp_server_info* info) {

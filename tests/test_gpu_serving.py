@@ -214,3 +214,33 @@ def test_light_load_uses_the_single_query_path(ahpp, tiny):
         srv.stop()
     check_same(r2, alone, k)
     assert r2.stats["rounds"] == alone.stats["rounds"]
+
+
+def test_cancel_queued_and_in_flight(ahpp, tiny):
+    """A cancelled queued request and a cancelled request on the device both
+    end with AHPP_ECANCELED (or their result if they finished first); the
+    other requests are unaffected and equal the query alone."""
+    G = tiny["G"]
+    srv = ahpp.Server(G, max_slots=32, rounds_per_step=1, single_max=-1)
+    try:
+        qs = synth.draw_queries(tiny["g"].n_u, 80, seed=91)
+        t = [srv.submit(int(q), 1e-8, 10) for q in qs]     # 32 on the device, 48 queued
+        assert srv.cancel(t[70]) == 0                        # still queued
+        for _ in range(2000):                                # wait until the first slots run
+            if srv.info()["in_flight"] > 0:
+                break
+            time.sleep(0.001)
+        assert srv.cancel(t[3]) == 0                         # on the device (or already done)
+        res = {i: srv.wait(t[i], 10) for i in range(80)}
+        assert res[70].rc == ahpp.AHPP_ECANCELED and res[70].nodes.shape[0] == 0
+        assert res[3].rc in (ahpp.AHPP_ECANCELED, 0)
+        with pytest.raises(ahpp.AhppError):
+            srv.cancel(t[5])                                 # delivered already
+        info = srv.info()
+        assert info["in_flight"] == 0 and info["queued"] == 0
+    finally:
+        srv.stop()
+    for i in (0, 4, 40, 79):
+        assert res[i].rc == 0
+        alone = G.query(int(qs[i]), 1e-8, 10)
+        check_same(res[i], alone, 10)
