@@ -144,6 +144,20 @@ const char *ahpp_last_error(void);
  * counts >= 2^31), AHPP_ENOMEM (budget or allocation), AHPP_ECUDA. */
 int ahpp_load_graph(const ahpp_graph_desc *desc, const ahpp_config *cfg, ahpp_graph **out);
 
+/* Graph cache.  ahpp_save_graph writes a loaded graph to `path`: its device
+ * arrays after duplicate merging, relabelling and the adjacency build, the
+ * normalisers and coefficients (Eq. 1, Eq. 2), the work items, and the lambda
+ * estimate (Theorem 3).  ahpp_load_graph_file reads such a file onto
+ * cfg->device without redoing that work; cfg's alpha, beta and attr_bf16
+ * must equal the cached graph's (the coefficients depend on them), the other
+ * fields apply as in ahpp_load_graph.  lambda: cfg->lambda if > 0, else the
+ * cached estimate if it was taken with the same lambda_T, else a new one.
+ * The file is in native byte order for the same build of this library.
+ * Errors: AHPP_EINVAL (null argument, unreadable, truncated or foreign file,
+ * mismatched alpha / beta / attr_bf16), AHPP_ENOMEM, AHPP_ECUDA. */
+int ahpp_save_graph(ahpp_graph *g, const char *path);
+int ahpp_load_graph_file(const char *path, const ahpp_config *cfg, ahpp_graph **out);
+
 /* Release every device and host resource of g (NULL is ignored). */
 void ahpp_free_graph(ahpp_graph *g);
 

@@ -88,6 +88,8 @@ SIGNATURES = {
     "ahpp_last_error": (ctypes.c_char_p, []),
     "ahpp_load_graph": (ctypes.c_int, [ctypes.POINTER(GraphDesc), ctypes.POINTER(Config),
                                        ctypes.POINTER(_vp)]),
+    "ahpp_save_graph": (ctypes.c_int, [_vp, ctypes.c_char_p]),
+    "ahpp_load_graph_file": (ctypes.c_int, [ctypes.c_char_p, ctypes.POINTER(Config), ctypes.POINTER(_vp)]),
     "ahpp_free_graph": (None, [_vp]),
     "ahpp_get_graph_info": (ctypes.c_int, [_vp, ctypes.POINTER(GraphInfo)]),
     "ahpp_query": (ctypes.c_int, [_vp, ctypes.c_uint32, ctypes.c_double, ctypes.c_uint32,
@@ -195,6 +197,21 @@ class Graph:
         self._h = h
         self._keep = None
         self.info = self.get_info()
+
+    @classmethod
+    def load_file(cls, path: str, **cfg) -> "Graph":
+        """A graph saved by save(); alpha, beta and attr_bf16 must match it."""
+        self = cls.__new__(cls)
+        self.config = default_config(**cfg)
+        h = _vp()
+        _check(lib().ahpp_load_graph_file(os.fsencode(path), ctypes.byref(self.config), ctypes.byref(h)))
+        self._h = h
+        self._keep = None
+        self.info = self.get_info()
+        return self
+
+    def save(self, path: str) -> None:
+        _check(lib().ahpp_save_graph(self._h, os.fsencode(path)))
 
     @classmethod
     def from_arrays(cls, g, **cfg) -> "Graph":

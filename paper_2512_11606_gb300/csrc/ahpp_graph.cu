@@ -383,8 +383,6 @@ int build_graph(const ahpp_graph_desc* d, ahpp_graph* g) {
   up_items(i1v, G.s1_v); up_items(i1a, G.s1_a); up_items(i1u, G.s1_u);
   up_items(ibv, G.b_v); up_items(iba, G.b_a); up_items(ibu, G.b_u);
   up_items(imv, G.m_v); up_items(ima, G.m_a); up_items(imu, G.m_u);
-  g->graph_bytes = 0;
-  for (auto& b : g->bufs) g->graph_bytes += b.bytes;
 
   g->h_u_old2new = u_o2n;
   g->h_u_new2old = u_n2o;
@@ -394,7 +392,18 @@ int build_graph(const ahpp_graph_desc* d, ahpp_graph* g) {
     if (!b.p) { set_error("ahpp_load_graph: device allocation failed"); return AHPP_ENOMEM; }
   if (cudaGetLastError() != cudaSuccess) { set_error("ahpp_load_graph: upload failed"); return AHPP_ECUDA; }
 
-  // 7. single-query state
+  g->n_graph_bufs = g->bufs.size();
+  g->graph_bytes = 0;
+  for (auto& b : g->bufs) g->graph_bytes += b.bytes;
+  return alloc_query_state(g);
+}
+
+// Single-query state of a loaded graph (working vectors, lists, accumulators,
+// barrier, trace) and the launch grid of the single-query kernel.
+int alloc_query_state(ahpp_graph* g) {
+  const ahpp_config& cfg = g->cfg;
+  const DevGraph& G = g->dg;
+  const uint32_t nU = G.n_u, nV = G.n_v, nA = G.n_a;
   g->n_split1 = G.s1_v.n_split + G.s1_a.n_split + G.s1_u.n_split;
   const size_t before = g->bufs.size();
   Q1State& s = g->q1;

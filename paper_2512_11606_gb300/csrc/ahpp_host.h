@@ -83,6 +83,7 @@ struct ahpp_graph {
 
   ahpp::DevGraph dg{};
   std::vector<ahpp::DevBuf> bufs;   // everything allocated for the graph
+  size_t n_graph_bufs = 0;          // bufs[0, n_graph_bufs): the graph's own arrays (what a cache saves)
   uint64_t graph_bytes = 0;
 
   // internal <-> caller id maps of U
@@ -112,6 +113,7 @@ struct ahpp_graph {
 
 namespace ahpp {
 int build_graph(const ahpp_graph_desc* desc, ahpp_graph* g);
+int alloc_query_state(ahpp_graph* g);
 int run_lambda(ahpp_graph* g);
 int run_query1(ahpp_graph* g, uint32_t q_new, double eps, uint32_t lambda_T_mode,
                cudaStream_t stream, QCtl* h_ctl);

@@ -191,3 +191,53 @@ def test_device_wait_gives_up_and_context_survives(ahpp, tiny):
     assert gave_up == 2 and ctx_ok
     r = tiny["G"].query(3, 1e-4, 5)
     assert r.rc == 0 and r.nodes.shape[0] == 5
+
+
+def test_graph_cache_round_trip(ahpp, tiny, tmp_path):
+    """A saved graph loads back without the build: same sizes and lambda,
+    same results; mismatched alpha and damaged files are refused."""
+    G, g = tiny["G"], tiny["g"]
+    path = str(tmp_path / "tiny.ahppg")
+    G.save(path)
+    H = ahpp.Graph.load_file(path, attr_bf16=0, lam=tiny["lam"])
+    try:
+        for key in ("n_u", "n_v", "n_a", "n_e", "n_ea", "graph_bytes", "lambda"):
+            assert H.info[key] == G.info[key], key
+        qs = [int(x) for x in synth.draw_queries(g.n_u, 40, seed=95)]
+        a, sa, _ = G.query_batch_dense(qs, 1e-6)
+        b, sb, rc = H.query_batch_dense(qs, 1e-6)
+        assert rc == 0 and np.abs(a - b).max() <= 1e-7
+        assert [s["rounds"] for s in sa] == [s["rounds"] for s in sb]
+        one = H.query(qs[0], 1e-6, 20)
+        check = G.query(qs[0], 1e-6, 20)
+        assert len(set(one.nodes.tolist()) & set(check.nodes.tolist())) >= 19
+    finally:
+        H.close()
+    with pytest.raises(ahpp.AhppError) as e:
+        ahpp.Graph.load_file(path, attr_bf16=0, lam=tiny["lam"], alpha=0.2)
+    assert e.value.code == ahpp.AHPP_EINVAL
+    data = open(path, "rb").read()
+    bad = str(tmp_path / "cut.ahppg")
+    open(bad, "wb").write(data[: len(data) // 2])
+    with pytest.raises(ahpp.AhppError) as e:
+        ahpp.Graph.load_file(bad, attr_bf16=0, lam=tiny["lam"])
+    assert e.value.code == ahpp.AHPP_EINVAL
+    with pytest.raises(ahpp.AhppError):
+        ahpp.Graph.load_file(str(tmp_path / "missing.ahppg"), attr_bf16=0, lam=tiny["lam"])
+
+
+def test_graph_cache_keeps_the_lambda_estimate(ahpp, tmp_path):
+    """A graph loaded with the Theorem 3 estimate keeps it through the cache
+    (no new lambda run) when loaded with the same lambda_T."""
+    g = synth.make_graph(**synth.TINY)
+    G = ahpp.Graph.from_arrays(g, attr_bf16=0)
+    path = str(tmp_path / "lam.ahppg")
+    try:
+        G.save(path)
+        H = ahpp.Graph.load_file(path, attr_bf16=0)
+        try:
+            assert H.info["lambda"] == G.info["lambda"] and H.info["lambda_T"] == G.info["lambda_T"]
+        finally:
+            H.close()
+    finally:
+        G.close()
