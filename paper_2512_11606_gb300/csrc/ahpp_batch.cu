@@ -139,6 +139,15 @@ __device__ __forceinline__ void st_keep4(float* p, float4 v) {
 #endif
 }
 
+// out[0..3] += v as a reduction that returns nothing: an atomicAdd on a
+// float4 whose result is unused is still issued as a returning atomic, and
+// the returned line then takes L2 -> SM bandwidth that the gathers need.
+__device__ __forceinline__ void red_add4(float* out, float4 v) {
+  asm volatile("red.global.add.v4.f32 [%0], {%1, %2, %3, %4};" ::"l"(out), "f"(v.x), "f"(v.y), "f"(v.z),
+               "f"(v.w)
+               : "memory");
+}
+
 __device__ __forceinline__ float4 f4_fma(float c, float4 x, float4 a) {
   return make_float4(fmaf(c, x.x, a.x), fmaf(c, x.y, a.y), fmaf(c, x.z, a.z), fmaf(c, x.w, a.w));
 }
@@ -247,7 +256,7 @@ __device__ __forceinline__ void flush_q4(Q4Partials& p, RAcc* acc) {
 __device__ __forceinline__ bool split_combine4(const TileBuf& t, uint32_t slot, uint32_t nch,
                                                float4 s, uint32_t gl, unsigned gmask, float4* tot) {
   float* a = &t.split_acc[(size_t)slot * kTile + kQL * gl];
-  atomicAdd(reinterpret_cast<float4*>(a), s);
+  red_add4(a, s);
   __threadfence();
   __syncwarp(gmask);
   uint32_t last = 0;
@@ -450,8 +459,7 @@ __device__ __forceinline__ void push_attr(const DevGraph& g, uint32_t u, float4 
       const uint32_t a = __shfl_sync(gmask, mi, t, kGL);
       const float cf = __shfl_sync(gmask, mc, t, kGL);
       if ((uint32_t)t < n && mine)
-        atomicAdd(reinterpret_cast<float4*>(ta_push + (size_t)a * kTile + kQL * gl),
-                  make_float4(cf * p.x, cf * p.y, cf * p.z, cf * p.w));
+        red_add4(ta_push + (size_t)a * kTile + kQL * gl, make_float4(cf * p.x, cf * p.y, cf * p.z, cf * p.w));
     }
   }
 }
