@@ -435,15 +435,14 @@ __device__ __forceinline__ float4 gepilogue2(const BCtx& c, uint32_t u, float4 s
 
 // Attribute hop of the coming round, pushed as soon as u is marked: for every
 // a in A(u), t_A'[a] += k_attr cnorm_a[a] w(u,a) rnorm_u[u] p_u (Eq. 2's two
-// factors and Algorithm 3's U-push share), one float4 atomic per lane and
-// attribute; t_A' is small enough to stay in L2.
+// factors and Algorithm 3's U-push share, precomputed per entry as ua_pc), one
+// float4 reduction per lane and attribute; t_A' is small enough to stay in L2.
 template <typename WA>
 __device__ __forceinline__ void push_attr(const DevGraph& g, uint32_t u, float4 p, float* ta_push,
                                           uint32_t gl, unsigned gmask) {
   const bool mine = p.x > 0.f || p.y > 0.f || p.z > 0.f || p.w > 0.f;
   if (!__any_sync(gmask, mine)) return;               // group-uniform
   const uint32_t b = g.ua_off[u], e = g.ua_off[u + 1];
-  const float f = g.k_attr * g.rnorm_u[u];
   // waves of kGL entries (one per lane of the group, coalesced); every lane
   // then issues one float4 reduction per entry for its 4 queries
   for (uint32_t k0 = b; k0 < e; k0 += kGL) {
@@ -452,7 +451,7 @@ __device__ __forceinline__ void push_attr(const DevGraph& g, uint32_t u, float4 
     float mc = 0.f;
     if (gl < n) {
       mi = g.ua_idx[k0 + gl];
-      mc = f * wload<WA>(g.ua_w, k0 + gl) * g.cnorm_a[mi];
+      mc = ld_stream(g.ua_pc + k0 + gl);
     }
 #pragma unroll
     for (int t = 0; t < kGL; ++t) {
@@ -903,11 +902,8 @@ k_tiles(const __grid_constant__ DevGraph g, const __grid_constant__ BatchState s
         a0->marked_deg = cnt;
         // the source's attribute push of the first round (see push_attr)
         float* ta_cur = (tround & 1) ? tb.t_a2 : tb.t_a;
-        const float f = g.k_attr * g.rnorm_u[q_new];
-        for (uint32_t k = g.ua_off[q_new]; AHPP_ATTR_PUSH && k < g.ua_off[q_new + 1]; ++k) {
-          const uint32_t a = g.ua_idx[k];
-          ta_cur[(size_t)a * kTile + lane] += f * wload<WA>(g.ua_w, k) * g.cnorm_a[a];
-        }
+        for (uint32_t k = g.ua_off[q_new]; AHPP_ATTR_PUSH && k < g.ua_off[q_new + 1]; ++k)
+          ta_cur[(size_t)g.ua_idx[k] * kTile + lane] += g.ua_pc[k];
       } else {
         tb.r_u[(size_t)q_new * kTile + lane] = 1.f;
       }

@@ -296,6 +296,17 @@ int build_graph(const ahpp_graph_desc* d, ahpp_graph* g) {
   std::vector<float> rnorm(nU), cnorm(nA);
   for (uint32_t u = 0; u < nU; ++u) rnorm[u] = wr[u] > 0 ? (float)(1.0 / wr[u]) : 0.f;
   for (uint32_t a = 0; a < nA; ++a) cnorm[a] = wc[a] > 0 ? (float)(1.0 / wc[a]) : 0.f;
+  // push coefficient of the U->A direction (both factors of Eq. 2 and the
+  // (1 - alpha) beta share of the U-push), rounded once to FP32
+  std::vector<float> f_ua_pc(ua_w.size());
+  const double ka = (1.0 - alpha) * beta;
+  parallel_for(nU, [&](size_t b, size_t e) {
+    for (size_t u = b; u < e; ++u)
+      for (uint32_t k = ua_off[u]; k < ua_off[u + 1]; ++k) {
+        const uint32_t a = ua_idx[k];
+        f_ua_pc[k] = (wr[u] > 0 && wc[a] > 0) ? (float)(ka * ua_w[k] / (wr[u] * wc[a])) : 0.f;
+      }
+  });
   // pull coefficient of the A->U direction (the U-side factor of Eq. 2), from
   // the quantised weight and the FP64 row sum, rounded once to FP32
   std::vector<float> f_au_c(au_w.size());
@@ -371,6 +382,7 @@ int build_graph(const ahpp_graph_desc* d, ahpp_graph* g) {
     G.au_mid = (const uint32_t*)up(amid.data(), amid.size() * 4);
   }
   G.au_c = (const float*)up(f_au_c.data(), f_au_c.size() * 4);
+  G.ua_pc = (const float*)up(f_ua_pc.data(), f_ua_pc.size() * 4);
   G.rnorm_u = (const float*)up(rnorm.data(), rnorm.size() * 4);
   G.cnorm_a = (const float*)up(cnorm.data(), cnorm.size() * 4);
   auto up_items = [&](const HostItems& h, ItemList& L) {

@@ -56,6 +56,7 @@ struct DevGraph {
   const uint32_t *au_off = nullptr, *au_idx = nullptr;
   const void* au_w = nullptr;
   const float* au_c = nullptr;          // A->U pull coefficient w(u,a) / sum_a' w(u,a') (FP32)
+  const float* ua_pc = nullptr;         // U->A push coefficient (1-alpha) beta w(u,a) / (sum_a' w(u,a') sum_u' w(u',a))
   const float* rnorm_u = nullptr;
   const float* cnorm_a = nullptr;
   // first entry of each V->U / A->U row whose U id is >= u_half (rows are
