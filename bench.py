@@ -235,16 +235,16 @@ def round_bytes(info, lanes, bf16=True):
 
     Graph (once per round, shared by the lanes): phase 1 streams V->U (index
     + coefficient, 8 B/edge); phase 2 streams U->V (index + weight, 8 B/edge)
-    and U->A once (index + bf16 weight, 6 B/entry; the attribute push reuses
-    the entries the gather read); row offsets of the three directions and the
-    U-side attribute normaliser.  State (per lane): phase 1 reads r_U once,
-    writes t_V, scans t_A and clears the next t_A; phase 2 reads t_V and t_A
-    once, reads and writes r_U, and read-modify-writes the reserve and its
+    and U->A (index + bf16 weight for the gather, FP32 push coefficient for the
+    attribute push: 10 B/entry; the push re-reads the index the gather read);
+    row offsets of the three directions.  State (per lane): phase 1 reads r_U
+    once, writes t_V, scans t_A and clears the next t_A; phase 2 reads t_V and
+    t_A once, reads and writes r_U, and read-modify-writes the reserve and its
     Kahan compensation.
     """
     wa = 2 if bf16 else 4
     nU, nV, nA, nE, nEA = (info[k] for k in ("n_u", "n_v", "n_a", "n_e", "n_ea"))
-    graph = 2 * (4 + 4) * nE + (4 + wa) * nEA + 4 * (2 * (nU + 1) + nV + 1) + 4 * nU + 4 * nA
+    graph = 2 * (4 + 4) * nE + (4 + wa + 4) * nEA + 4 * (2 * (nU + 1) + nV + 1)
     state = lanes * 4 * (nU + nV + 2 * nA + nV + nA + 2 * nU + 4 * nU)
     return graph + state
 
