@@ -254,16 +254,16 @@ def topk_bytes(info, queries):
 
 
 # DRAM bytes (read + write) per tile-round of k_tiles on the medium graph, from
-# the ncu capture summarised in profiles/k_tiles_medium_tile32.md (245.25 GB over
+# the ncu capture summarised in profiles/k_tiles_medium_tile32.md (257.40 GB over
 # the 106 rounds of one 32-query tile).  It describes the kernel built from the
 # sources listed by hash; once any of them changes the figure no longer applies.
 NCU_TRAFFIC = {
     "graph": "medium",
-    "bytes_per_tile_round": 245.25e9 / 106,
+    "bytes_per_tile_round": 257.40e9 / 106,
     # l1tex__m_xbar2l1tex_read_bytes.sum of the same capture: bytes moved from L2 to the SMs
-    "l2_to_sm_bytes_per_tile_round": 1.257359e12 / 106,
-    "sources": {"ahpp_batch.cu": "0883468643b2ceda", "ahpp_batch.cuh": "f3dfbbd4287bd668",
-                "ahpp_internal.cuh": "64c85a4429923409"},
+    "l2_to_sm_bytes_per_tile_round": 944.894883e9 / 106,
+    "sources": {"ahpp_batch.cu": "de4b77bce76bf143", "ahpp_batch.cuh": "f3dfbbd4287bd668",
+                "ahpp_internal.cuh": "b85a585f011dc3c6"},
 }
 
 
