@@ -583,15 +583,55 @@ def run_ablation(ahpp, g, args, lam, device):
     return out
 
 
-def run_serving(ahpp, G, g, args, rate):
-    """Continuous batching through the server API, two measurements.
+def closed_loop(srv, qs, eps, ks, inflight):
+    """Keep `inflight` requests submitted: take results in submit order and
+    submit the next request as each result is taken.  Returns the completion
+    times (s from the first submit), latencies (ms) and rounds per request."""
+    n = len(qs)
+    pending = [(srv.submit(int(qs[i]), float(eps[i]), int(ks[i])), int(ks[i])) for i in range(min(inflight, n))]
+    nxt = len(pending)
+    done_t, lat, rounds = [], [], []
+    t0 = time.perf_counter()
+    while pending:
+        t, kk = pending.pop(0)
+        r = srv.wait(t, kk)
+        done_t.append(time.perf_counter() - t0)
+        lat.append(r.stats["served_ms"])
+        rounds.append(r.stats["rounds"])
+        if nxt < n:
+            pending.append((srv.submit(int(qs[nxt]), float(eps[nxt]), int(ks[nxt])), int(ks[nxt])))
+            nxt += 1
+    return done_t, lat, rounds
 
-    saturated: closed loop with as many requests in flight as slots (a new
-    request is submitted as each result is taken); completed queries/s and
-    submit-to-result latency over a steady-state window (ramp-up and drain
-    excluded).
-    open_loop: Poisson arrivals at `rate` queries/s for args.serve_seconds;
-    completed queries/s and latency percentiles of every request.
+
+def steady_state(done_t, lat, inflight):
+    """qps and latency over the window after the first wave and before the
+    drain (None when the run is too short for one)."""
+    n = len(done_t)
+    lo, hi = inflight, n - inflight
+    if hi - lo < 8:
+        return None
+    return {
+        "qps": (hi - lo) / (done_t[hi - 1] - done_t[lo - 1]),
+        "p50_ms": statistics.median(lat[lo:hi]),
+        "p99_ms": float(np.percentile(lat[lo:hi], 99)),
+        "queries": n, "window_queries": hi - lo, "in_flight": inflight,
+    }
+
+
+def run_serving(ahpp, G, g, args, rate):
+    """Continuous batching through the server API.
+
+    saturated: closed loop with every slot busy and as many requests queued
+    besides (lanes that all finish in one step are refilled at the next
+    step), so the queue never runs dry; completed
+    queries/s and submit-to-result latency over a steady-state window
+    (ramp-up and drain excluded).  saturated_short_queue: the same with only
+    a quarter of the slots queued (lower latency; lanes that finish together wait a
+    step for requests the clients have not yet resubmitted).  saturated_mix:
+    as saturated, with the serving workload's per-request eps and k.
+    open_loop_light / open_loop: Poisson arrivals at 5 % of capacity and at
+    `rate` queries/s; completed queries/s and latency percentiles.
     """
     out = {"slots": None, "rounds_per_step": args.serve_rounds}
     srv = ahpp.Server(G, max_slots=args.serve_slots, rounds_per_step=args.serve_rounds)
@@ -602,67 +642,42 @@ def run_serving(ahpp, G, g, args, rate):
         for t in warm:
             srv.wait(t, args.k)
 
-        # saturated (closed loop): every slot busy plus a small queued backlog,
-        # so that a slot freed at a step is refilled at the next step
         n_sat = max(4 * slots, int(args.serve_seconds * rate / max(args.serve_load, 1e-3) / 2))
-        inflight = slots + max(4, slots // 4)
+        full_q = 2 * slots        # every slot busy, as many queued: all slots may finish in one step
+        short_q = slots + max(4, slots // 4)
+        eps_u = np.full(n_sat, args.eps)
+        k_u = np.full(n_sat, args.k)
+
         qs = synth.draw_queries(g.n_u, n_sat, seed=202)
         clk = ClockSampler(gpu_index(G.info["device"]))
         clk.start()
-        pending = [srv.submit(int(q), args.eps, args.k) for q in qs[:inflight]]
-        nxt = inflight
-        done_t, lat = [], []
-        t0 = time.perf_counter()
-        while pending:
-            r = srv.wait(pending.pop(0), args.k)
-            done_t.append(time.perf_counter() - t0)
-            lat.append(r.stats["served_ms"])
-            if nxt < n_sat:
-                pending.append(srv.submit(int(qs[nxt]), args.eps, args.k))
-                nxt += 1
+        done_t, lat, _ = closed_loop(srv, qs, eps_u, k_u, full_q)
         sat_clocks = clk.stop()
-        lo, hi = inflight, n_sat - inflight    # steady state: after the first wave, before the drain
-        if hi - lo >= 8:
-            out["saturated"] = {
-                "qps": (hi - lo) / (done_t[hi - 1] - done_t[lo - 1]),
-                "p50_ms": statistics.median(lat[lo:hi]),
-                "p99_ms": float(np.percentile(lat[lo:hi], 99)),
-                "queries": n_sat, "window_queries": hi - lo,
-                "in_flight": inflight,
-                "clocks": sat_clocks,
-                "note": "closed loop, requests in flight = slots + a queued backlog; qps over the steady-state window",
-            }
+        sat = steady_state(done_t, lat, full_q)
+        if sat:
+            sat["clocks"] = sat_clocks
+            sat["note"] = ("closed loop, requests in flight = 2 x slots (the queue never runs dry); "
+                           "qps over the steady-state window; latency includes the queue wait")
+            out["saturated"] = sat
 
-        # saturated with the serving workload's request mix: eps log-uniform in
-        # [1e-7, 1e-4], k in {10, 100, 1000} (per-request eps and k in one tile)
+        done_t, lat, _ = closed_loop(srv, qs, eps_u, k_u, short_q)
+        short = steady_state(done_t, lat, short_q)
+        if short:
+            short["note"] = "closed loop, requests in flight = slots + a quarter of them queued"
+            out["saturated_short_queue"] = short
+
+        # the serving workload's request mix: eps log-uniform in [1e-7, 1e-4],
+        # k in {10, 100, 1000} (per-request eps and k in one tile)
         rng = np.random.default_rng(404)
-        n_mix = n_sat
-        qm = synth.draw_queries(g.n_u, n_mix, seed=405)
-        em = np.exp(rng.uniform(np.log(1e-7), np.log(1e-4), n_mix))
-        km = rng.choice([10, 100, 1000], n_mix)
-        pending = [(srv.submit(int(qm[i]), float(em[i]), int(km[i])), int(km[i])) for i in range(inflight)]
-        nxt = inflight
-        done_t, lat, rounds = [], [], []
-        t0 = time.perf_counter()
-        while pending:
-            t, kk = pending.pop(0)
-            r = srv.wait(t, kk)
-            done_t.append(time.perf_counter() - t0)
-            lat.append(r.stats["served_ms"])
-            rounds.append(r.stats["rounds"])
-            if nxt < n_mix:
-                pending.append((srv.submit(int(qm[nxt]), float(em[nxt]), int(km[nxt])), int(km[nxt])))
-                nxt += 1
-        lo, hi = inflight, n_mix - inflight
-        if hi - lo >= 8:
-            out["saturated_mix"] = {
-                "qps": (hi - lo) / (done_t[hi - 1] - done_t[lo - 1]),
-                "p50_ms": statistics.median(lat[lo:hi]),
-                "p99_ms": float(np.percentile(lat[lo:hi], 99)),
-                "rounds_mean": float(np.mean(rounds)),
-                "queries": n_mix,
-                "note": "closed loop as above; eps log-uniform in [1e-7, 1e-4], k in {10, 100, 1000}",
-            }
+        qm = synth.draw_queries(g.n_u, n_sat, seed=405)
+        em = np.exp(rng.uniform(np.log(1e-7), np.log(1e-4), n_sat))
+        km = rng.choice([10, 100, 1000], n_sat)
+        done_t, lat, rounds = closed_loop(srv, qm, em, km, full_q)
+        mix = steady_state(done_t, lat, full_q)
+        if mix:
+            mix["rounds_mean"] = float(np.mean(rounds))
+            mix["note"] = "closed loop as saturated; eps log-uniform in [1e-7, 1e-4], k in {10, 100, 1000}"
+            out["saturated_mix"] = mix
 
         # light load: Poisson arrivals at 5 % of the batched capacity; the server
         # answers most requests on the single-query path

@@ -53,3 +53,42 @@ def test_ncu_traffic_applies_only_to_the_captured_sources(monkeypatch):
     monkeypatch.setattr(bench, "NCU_TRAFFIC", bad)
     assert bench.ncu_traffic("medium", 10) is None
     assert bench.ncu_traffic("medium", 10, "l2_to_sm_bytes_per_tile_round") is None
+
+
+class FakeServer:
+    """Answers in submit order; records how many requests were outstanding
+    at each submit."""
+
+    def __init__(self):
+        self.next, self.out, self.peak = 0, set(), 0
+        self.args = {}
+
+    def submit(self, q, eps, k):
+        t = self.next
+        self.next += 1
+        self.out.add(t)
+        self.peak = max(self.peak, len(self.out))
+        self.args[t] = (q, eps, k)
+        return t
+
+    def wait(self, t, k):
+        self.out.discard(t)
+        q, eps, kk = self.args[t]
+        assert kk == k
+
+        class R:
+            stats = {"served_ms": float(t), "rounds": q}
+        return R
+
+
+def test_closed_loop_keeps_the_backlog_and_order():
+    srv = FakeServer()
+    n, inflight = 100, 64
+    qs = list(range(1000, 1000 + n))
+    done_t, lat, rounds = bench.closed_loop(srv, qs, [1e-6] * n, [10 + i % 3 for i in range(n)], inflight)
+    assert srv.peak == inflight and srv.next == n
+    assert lat == [float(i) for i in range(n)] and rounds == qs
+    assert all(b >= a for a, b in zip(done_t, done_t[1:]))
+    s = bench.steady_state(done_t, lat, 40)
+    assert s["window_queries"] == 20 and s["in_flight"] == 40
+    assert bench.steady_state(done_t, lat, 48) is None
