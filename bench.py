@@ -604,18 +604,33 @@ def closed_loop(srv, qs, eps, ks, inflight):
     return done_t, lat, rounds
 
 
-def steady_state(done_t, lat, inflight):
+def burst_end(done_t, i, gap_s):
+    """The last index of the burst of completions that index i belongs to
+    (results of one server step arrive together; a gap above gap_s starts
+    the next burst)."""
+    while i + 1 < len(done_t) and done_t[i + 1] - done_t[i] <= gap_s:
+        i += 1
+    return i
+
+
+def steady_state(done_t, lat, inflight, gap_s=1e-3):
     """qps and latency over the window after the first wave and before the
-    drain (None when the run is too short for one)."""
+    drain (None when the run is too short for one).  Both window edges are
+    moved to the end of a burst, so the window spans whole server steps: an
+    edge inside a burst would count up to a whole step's results against a
+    fraction of its time."""
     n = len(done_t)
     lo, hi = inflight, n - inflight
     if hi - lo < 8:
         return None
+    a, b = burst_end(done_t, lo - 1, gap_s), burst_end(done_t, hi - 1, gap_s)
+    if b - a < 8:
+        a, b = lo - 1, hi - 1
     return {
-        "qps": (hi - lo) / (done_t[hi - 1] - done_t[lo - 1]),
-        "p50_ms": statistics.median(lat[lo:hi]),
-        "p99_ms": float(np.percentile(lat[lo:hi], 99)),
-        "queries": n, "window_queries": hi - lo, "in_flight": inflight,
+        "qps": (b - a) / (done_t[b] - done_t[a]),
+        "p50_ms": statistics.median(lat[a + 1:b + 1]),
+        "p99_ms": float(np.percentile(lat[a + 1:b + 1], 99)),
+        "queries": n, "window_queries": b - a, "in_flight": inflight,
     }
 
 

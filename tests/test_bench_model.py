@@ -92,3 +92,18 @@ def test_closed_loop_keeps_the_backlog_and_order():
     s = bench.steady_state(done_t, lat, 40)
     assert s["window_queries"] == 20 and s["in_flight"] == 40
     assert bench.steady_state(done_t, lat, 48) is None
+
+
+def test_steady_state_counts_whole_bursts():
+    """Results of one server step arrive together: 32 every 5 ms is 6,400
+    queries/s, whichever index the window would start and end at."""
+    burst, period, n_bursts = 32, 5e-3, 40
+    done_t = [b * period + j * 50e-6 for b in range(n_bursts) for j in range(burst)]
+    lat = [1.0] * len(done_t)
+    for inflight in (40, 47, 64, 70):
+        s = bench.steady_state(done_t, lat, inflight)
+        assert s["qps"] == pytest.approx(burst / period, rel=1e-9)
+        assert s["window_queries"] % burst == 0
+    # without the snapping, window edges inside bursts read off the rate
+    lo, hi = 40, len(done_t) - 40
+    assert abs((hi - lo) / (done_t[hi - 1] - done_t[lo - 1]) / (burst / period) - 1) > 0.005
