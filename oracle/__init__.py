@@ -18,9 +18,13 @@ Two layers:
 
 Parity status: every function here is pinned by the tests in
 ``tests/test_oracle_*.py`` (worked example of Section 2.1, closed forms,
-Lemma 1 sampling, Lemma 3 per round, Theorems 2 and 3), except the ASRP
-switch rule, whose trajectory the paper never prints: parity unpinned
-beyond the error guarantee and internal consistency.
+Lemma 1 sampling, Lemma 3 per round, Theorems 2 and 3).  The ASRP switch
+test of Algorithm 4 is printed in a garbled form; the oracle implements the
+reading that Theorem 1's proof supports (and the printed form as an
+option), and both are pinned by the trajectory worked out by hand on a
+graph with P = J/n (switch round, rounds, pushed entries, traces, reserves)
+and by the selection rule of each phase on a power-law graph.  No printed
+trajectory exists to pin the reading itself against.
 """
 from __future__ import annotations
 

@@ -131,6 +131,65 @@ def test_closed_form_uniform_chain(n):
         assert np.all(want - res.pi >= -1e-15) and np.all(want - res.pi <= eps * 1.0001)
 
 
+def hub_trajectory(n, eps, lam, rule):
+    """ASRP on the hub graph, worked out by hand.
+
+    Every round after the first pushes all n U nodes with equal residues, so
+    after round k each residue is (1-a)^k / n.  Round 1 pushes q alone: its
+    two entries plus the V and A flushes (n each) give n_p = 2n + 2; every
+    later round adds 2n pushed entries and 2n flushed ones, so
+    n_p(k) = 4nk - 2n + 2.  The loop ends after the first round R with
+    (1-a)^R / n <= eps_f (eps_f = eps / lam): R = ceil(L) with
+    L = log_{1/(1-a)} (1 / (n eps_f)).  The switch test after asynchronous
+    round k compares n_p(k) with the budget 2(|E| + |E_A|) = 4n times
+      rule 0 (the budget of Theorem 1's proof): max(0, L - k), which n_p(k)
+              reaches from k >= L/2 + 1/4 - 1/(4n) on;
+      rule 1 (the formula as printed): log_{1/(1-a)} (n / lam) + k, which
+              n_p(k) reaches at every k or at none: iff that log is at most
+              (1 - n) / (2n).
+    Returns (rounds, switch_round, the thresholds that decide them)."""
+    lg = math.log(1 / (1 - ALPHA))
+    L = math.log(lam / (n * eps)) / lg
+    R = math.ceil(L)
+    if rule == 0:
+        ks = max(1, math.ceil(L / 2 + 0.25 - 0.25 / n))
+        cuts = [L, L / 2 + 0.25 - 0.25 / n]
+    else:
+        L1 = math.log(n / lam) / lg
+        ks = 1 if L1 <= (1 - n) / (2 * n) else None
+        cuts = [L, L1 - (1 - n) / (2 * n)]
+    sr = ks + 1 if ks is not None and ks <= R else 0
+    return R, sr, cuts
+
+
+@pytest.mark.parametrize("n,eps,lam,rule", [(5, 1e-6, 3.0, 0), (17, 1e-9, 50.0, 0), (2, 1e-4, 1.5, 0),
+                                            (5, 1e-6, 100.0, 1), (5, 1e-6, 3.0, 1)])
+def test_asrp_trajectory_closed_form_on_hub_graph(n, eps, lam, rule):
+    """The ASRP switch and termination, n_p accounting, traces and the final
+    reserves on P = J/n against the trajectory derived by hand."""
+    R, sr, cuts = hub_trajectory(n, eps, lam, rule)
+    for c in cuts:              # no decision sits on a rounding boundary
+        assert abs(c - round(c)) > 1e-6 or abs(c) > 1e6
+    og = oracle.OracleGraph.from_arrays(hub_graph(n))
+    q = n // 2
+    res = og.push("asrp", ALPHA, BETA, q, eps, lam=lam, switch_rule=rule)
+    s, t = res.stats, res.trace
+    assert res.rc == 0
+    assert s["rounds"] == R and s["switch_round"] == sr
+    k = np.arange(1, R + 1)
+    assert t["frontier"].tolist() == [1] + [n] * (R - 1)
+    assert t["n_p"].tolist() == (4 * n * k - 2 * n + 2).tolist()
+    assert s["n_p"] == 4 * n * R - 2 * n + 2 and s["pushes"] == 1 + n * (R - 1)
+    np.testing.assert_allclose(t["max_r"], (1 - ALPHA) ** k / n, rtol=1e-12)
+    want_phase = [0] * R if sr == 0 else [0] * (sr - 1) + [1] * (R - sr + 1)
+    assert t["phase"].tolist() == want_phase[:R]
+    share = ALPHA * sum((1 - ALPHA) ** j for j in range(1, R)) / n
+    want = np.full(n, share)
+    want[q] += ALPHA
+    np.testing.assert_allclose(res.pi, want, rtol=1e-12)
+    np.testing.assert_allclose(res.r_u, np.full(n, (1 - ALPHA) ** R / n), rtol=1e-12)
+
+
 def small_random_graph(seed, n_u=8, n_v=6, n_e=18, n_a=4, m=2):
     rng = np.random.default_rng(seed)
     pairs = set()
@@ -328,6 +387,39 @@ def test_asrp_switch_and_termination_consistency(tiny):
     never = og.push("asrp", ALPHA, BETA, q, eps, lam=lam, switch_rule=2)
     assert never.stats["switch_round"] == 0
     np.testing.assert_allclose(never.pi, res.pi, atol=eps)
+
+
+def test_asrp_selection_rule_of_each_phase(tiny):
+    """Algorithm 4 pushes, in an asynchronous round, exactly the U nodes whose
+    residue exceeds eps_f and, in a synchronous round, every U node with a
+    positive residue.  The residues before round j come from a second run
+    stopped after j - 1 rounds."""
+    og, q, lam = tiny["og"], tiny["q"], tiny["lam"]
+    eps = 1e-6
+    eps_f = eps / lam
+    full = og.push("asrp", ALPHA, BETA, q, eps, lam=lam)
+    sr, R = full.stats["switch_round"], full.stats["rounds"]
+    assert 2 < sr < R
+    checked = {0: 0, 1: 0}
+    for j in sorted({2, 3, sr - 1, sr, sr + 1, R}):
+        before = og.push("asrp", ALPHA, BETA, q, eps, lam=lam, max_rounds=j - 1)
+        assert before.rc == 1 and before.stats["rounds"] == j - 1
+        sync = j >= sr
+        want = int((before.r_u > 0).sum()) if sync else int((before.r_u > eps_f).sum())
+        assert full.trace["frontier"][j - 1] == want, (j, sync)
+        checked[int(sync)] += 1
+    assert checked[0] and checked[1]
+    # near the end the synchronous frontier is wider than the asynchronous
+    # rule would give (positive residues at or below eps_f are pushed too)
+    wider = False
+    for j in range(R, max(sr, R - 6), -1):
+        before = og.push("asrp", ALPHA, BETA, q, eps, lam=lam, max_rounds=j - 1)
+        n_pos, n_above = int((before.r_u > 0).sum()), int((before.r_u > eps_f).sum())
+        assert full.trace["frontier"][j - 1] == n_pos
+        if n_pos > n_above:
+            wider = True
+            break
+    assert wider
 
 
 def test_topk_matches_sorting(tiny):
