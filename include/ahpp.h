@@ -152,9 +152,13 @@ int ahpp_load_graph(const ahpp_graph_desc *desc, const ahpp_config *cfg, ahpp_gr
  * must equal the cached graph's (the coefficients depend on them), the other
  * fields apply as in ahpp_load_graph.  lambda: cfg->lambda if > 0, else the
  * cached estimate if it was taken with the same lambda_T, else a new one.
- * The file is in native byte order for the same build of this library.
- * Errors: AHPP_EINVAL (null argument, unreadable, truncated or foreign file,
- * mismatched alpha / beta / attr_bf16), AHPP_ENOMEM, AHPP_ECUDA. */
+ * The file is in native byte order for the same build of this library and
+ * ends with a checksum of its contents; the loader checks the header, the
+ * buffer table, the length and the checksum but does not re-derive the
+ * arrays, so load only files that ahpp_save_graph wrote.
+ * Errors: AHPP_EINVAL (null argument, unreadable, truncated, damaged or
+ * foreign file, mismatched alpha / beta / attr_bf16), AHPP_ENOMEM,
+ * AHPP_ECUDA. */
 int ahpp_save_graph(ahpp_graph *g, const char *path);
 int ahpp_load_graph_file(const char *path, const ahpp_config *cfg, ahpp_graph **out);
 

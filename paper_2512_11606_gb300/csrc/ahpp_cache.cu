@@ -11,6 +11,11 @@
 //   DevGraph bytes (pointer fields meaningless), then for every pointer field
 //   of the graph, in a fixed order, the i64 index of its buffer (-1: null)
 //   for every buffer: u64 bytes, then the bytes
+//   u64 checksum of every byte above (Checksum below), then the end of file
+// The loader checks the header, the buffer table, the file length and the
+// checksum; it does not re-derive the arrays' contents, so it accepts only
+// files this library wrote (a checksum guards against accidental damage,
+// not against a file crafted to pass it).
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -23,7 +28,7 @@ namespace ahpp {
 namespace {
 
 constexpr char kMagic[8] = {'A', 'H', 'P', 'P', 'G', 'R', 'F', '1'};
-constexpr uint32_t kVersion = 2;
+constexpr uint32_t kVersion = 3;
 
 struct CacheHeader {
   char magic[8];
@@ -61,8 +66,38 @@ struct File {
   ~File() { if (f) fclose(f); }
 };
 
-bool wr(FILE* f, const void* p, size_t n) { return n == 0 || fwrite(p, 1, n, f) == n; }
-bool rd(FILE* f, void* p, size_t n) { return n == 0 || fread(p, 1, n, f) == n; }
+// Word-wise multiply-rotate checksum: each 8-byte word (then each tail byte)
+// is XORed in, rotated and multiplied by an odd constant.  Every step is a
+// bijection of the state, so a file that differs in one word or byte always
+// gives a different sum.  Save and load feed it the same sequence of chunks.
+struct Checksum {
+  uint64_t h = 0x243F6A8885A308D3ull;
+  void step(uint64_t w) {
+    h ^= w;
+    h = (h << 31) | (h >> 33);
+    h *= 0x9E3779B97F4A7C15ull;
+  }
+  void add(const void* p, size_t n) {
+    const unsigned char* b = static_cast<const unsigned char*>(p);
+    size_t i = 0;
+    for (; i + 8 <= n; i += 8) {
+      uint64_t w;
+      std::memcpy(&w, b + i, 8);
+      step(w);
+    }
+    for (; i < n; ++i) step(b[i]);
+  }
+};
+
+bool wr(FILE* f, const void* p, size_t n, Checksum& cs) {
+  cs.add(p, n);
+  return n == 0 || fwrite(p, 1, n, f) == n;
+}
+bool rd(FILE* f, void* p, size_t n, Checksum& cs) {
+  if (n != 0 && fread(p, 1, n, f) != n) return false;
+  cs.add(p, n);
+  return true;
+}
 
 }  // namespace
 }  // namespace ahpp
@@ -96,15 +131,18 @@ extern "C" int ahpp_save_graph(ahpp_graph* g, const char* path) {
   h.alpha = g->cfg.alpha; h.beta = g->cfg.beta; h.lambda = g->lambda;
   h.lambda_T = g->lambda_T; h.attr_bf16 = g->bf16 ? 1u : 0u; h.algo = (uint32_t)g->cfg.algo;
   h.n_buffers = g->n_graph_bufs;
-  bool w = wr(out.f, &h, sizeof(h)) && wr(out.f, &g->dg, sizeof(DevGraph)) &&
-           wr(out.f, index.data(), index.size() * sizeof(int64_t));
+  Checksum cs;
+  bool w = wr(out.f, &h, sizeof(h), cs) && wr(out.f, &g->dg, sizeof(DevGraph), cs) &&
+           wr(out.f, index.data(), index.size() * sizeof(int64_t), cs);
   std::vector<unsigned char> host;
   for (size_t i = 0; w && i < g->n_graph_bufs; ++i) {
     const uint64_t n = g->bufs[i].bytes;
     host.resize(n);
     if (n) AHPP_CUDA(cudaMemcpy(host.data(), g->bufs[i].p, n, cudaMemcpyDeviceToHost));
-    w = wr(out.f, &n, sizeof(n)) && wr(out.f, host.data(), n);
+    w = wr(out.f, &n, sizeof(n), cs) && wr(out.f, host.data(), n, cs);
   }
+  const uint64_t sum = cs.h;
+  w = w && fwrite(&sum, 1, sizeof(sum), out.f) == sizeof(sum);
   if (!w || fflush(out.f) != 0) { set_error(std::string("ahpp_save_graph: write failed: ") + path); return AHPP_EINVAL; }
   return AHPP_OK;
 }
@@ -124,7 +162,8 @@ extern "C" int ahpp_load_graph_file(const char* path, const ahpp_config* cfg, ah
   }
   if (fseek(in.f, 0, SEEK_SET) != 0) { set_error("ahpp_load_graph_file: cannot read the file"); return AHPP_EINVAL; }
   CacheHeader h{};
-  if (!rd(in.f, &h, sizeof(h)) || std::memcmp(h.magic, kMagic, 8) != 0 || h.version != kVersion) {
+  Checksum cs;
+  if (!rd(in.f, &h, sizeof(h), cs) || std::memcmp(h.magic, kMagic, 8) != 0 || h.version != kVersion) {
     set_error("ahpp_load_graph_file: not a graph cache of this library version");
     return AHPP_EINVAL;
   }
@@ -175,25 +214,34 @@ extern "C" int ahpp_load_graph_file(const char* path, const ahpp_config* cfg, ah
   }
   std::vector<int64_t> index;
   visit_graph_ptrs(g, [&](const void**) { index.push_back(0); });
-  if (rc == AHPP_OK && (!rd(in.f, &g->dg, sizeof(DevGraph)) ||
-                        !rd(in.f, index.data(), index.size() * sizeof(int64_t))))
+  if (rc == AHPP_OK && (!rd(in.f, &g->dg, sizeof(DevGraph), cs) ||
+                        !rd(in.f, index.data(), index.size() * sizeof(int64_t), cs)))
     fail(AHPP_EINVAL, "ahpp_load_graph_file: truncated file");
   std::vector<unsigned char> host;
   for (uint64_t i = 0; rc == AHPP_OK && i < h.n_buffers; ++i) {
     uint64_t n = 0;
     const long at = ftell(in.f);
-    if (!rd(in.f, &n, sizeof(n)) || at < 0 || n > file_bytes - (uint64_t)at) {   // never past the file's end
+    if (!rd(in.f, &n, sizeof(n), cs) || at < 0 || n > file_bytes - (uint64_t)at) {   // never past the file's end
       fail(AHPP_EINVAL, "ahpp_load_graph_file: truncated file");
       break;
     }
     host.resize(n);
-    if (!rd(in.f, host.data(), n)) { fail(AHPP_EINVAL, "ahpp_load_graph_file: truncated file"); break; }
+    if (!rd(in.f, host.data(), n, cs)) { fail(AHPP_EINVAL, "ahpp_load_graph_file: truncated file"); break; }
     void* p = g->alloc(n ? n : 4);
     if (!p) { fail(AHPP_ENOMEM, "ahpp_load_graph_file: device allocation failed"); break; }
     if (n && cudaMemcpy(p, host.data(), n, cudaMemcpyHostToDevice) != cudaSuccess) {
       cudaGetLastError();
       fail(AHPP_ECUDA, "ahpp_load_graph_file: upload failed");
     }
+  }
+  if (rc == AHPP_OK) {
+    uint64_t sum = 0;
+    const bool got = fread(&sum, 1, sizeof(sum), in.f) == sizeof(sum);
+    const long end = ftell(in.f);
+    if (!got || end < 0 || (uint64_t)end != file_bytes)
+      fail(AHPP_EINVAL, "ahpp_load_graph_file: truncated file or trailing bytes");
+    else if (sum != cs.h)
+      fail(AHPP_EINVAL, "ahpp_load_graph_file: checksum mismatch (damaged file)");
   }
   if (rc == AHPP_OK) {
     size_t k = 0;

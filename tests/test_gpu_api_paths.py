@@ -195,7 +195,8 @@ def test_device_wait_gives_up_and_context_survives(ahpp, tiny):
 
 def test_graph_cache_round_trip(ahpp, tiny, tmp_path):
     """A saved graph loads back without the build: same sizes and lambda,
-    same results; mismatched alpha and damaged files are refused."""
+    same results; mismatched alpha and truncated, damaged or extended files
+    are refused."""
     G, g = tiny["G"], tiny["g"]
     path = str(tmp_path / "tiny.ahppg")
     G.save(path)
@@ -224,6 +225,17 @@ def test_graph_cache_round_trip(ahpp, tiny, tmp_path):
     assert e.value.code == ahpp.AHPP_EINVAL
     with pytest.raises(ahpp.AhppError):
         ahpp.Graph.load_file(str(tmp_path / "missing.ahppg"), attr_bf16=0, lam=tiny["lam"])
+    # one flipped byte in the arrays, or bytes after the checksum: refused
+    flipped = bytearray(data)
+    flipped[len(data) * 3 // 4] ^= 0x10
+    for name, blob in (("flip.ahppg", bytes(flipped)), ("tail.ahppg", data + b"\0" * 8)):
+        bad = str(tmp_path / name)
+        open(bad, "wb").write(blob)
+        with pytest.raises(ahpp.AhppError) as e:
+            ahpp.Graph.load_file(bad, attr_bf16=0, lam=tiny["lam"])
+        assert e.value.code == ahpp.AHPP_EINVAL
+    # the intact file still loads after the refusals
+    ahpp.Graph.load_file(path, attr_bf16=0, lam=tiny["lam"]).close()
 
 
 def test_graph_cache_keeps_the_lambda_estimate(ahpp, tmp_path):
