@@ -173,6 +173,25 @@ def test_asrp_trajectory_closed_form_on_hub_graph(n, eps, lam, rule):
     og = oracle.OracleGraph.from_arrays(hub_graph(n))
     q = n // 2
     res = og.push("asrp", ALPHA, BETA, q, eps, lam=lam, switch_rule=rule)
+    check_hub_run(res, n, q, R, sr)
+
+
+@pytest.mark.parametrize("n,eps", [(5, 1e-6), (17, 1e-9), (2, 3e-4)])
+def test_app_trajectory_closed_form_on_hub_graph(n, eps):
+    """APP on P = J/n: every U node has |N(u)| + |A(u)| = 2 and
+    r_max = eps / (|E| + |E_A|) = eps / (2n), so the threshold is eps / n and
+    the run ends after the first round R with (1-a)^R <= eps; the rounds
+    push as in ASRP's (n_p, traces, reserves) without a phase switch."""
+    L = math.log(1 / eps) / math.log(1 / (1 - ALPHA))
+    assert abs(L - round(L)) > 1e-6
+    R = math.ceil(L)
+    og = oracle.OracleGraph.from_arrays(hub_graph(n))
+    q = n - 1
+    res = og.push("app", ALPHA, BETA, q, eps)
+    check_hub_run(res, n, q, R, 0)
+
+
+def check_hub_run(res, n, q, R, sr):
     s, t = res.stats, res.trace
     assert res.rc == 0
     assert s["rounds"] == R and s["switch_round"] == sr
