@@ -350,6 +350,38 @@ def test_lambda_bounds_column_sums(tiny):
     assert tiny["lam"] <= colsum + 0.0101
 
 
+@pytest.mark.parametrize("n", [3, 11])
+def test_lambda_estimate_closed_form_on_weighted_hub(n):
+    """Theorem 3's estimate on a weighted hub: U node i joined to the one V
+    node with weight w_i and to the one attribute with weight x_i.  Then every
+    row of P is mu = (1-b) w/W + b x/X (Eq. 1 and Eq. 2 with one middle node),
+    so 1 P^l = n mu for l >= 1 and
+        pi_T = a + n mu ((1-a) - (1-a)^T),
+        lambda = max pi_T + n (1-a)^T,
+    with T = ceil(ln(100 n) / ln(1/(1-a))); the exact column sums of Pi are
+    a + (1-a) n mu, below lambda."""
+    rng = np.random.default_rng(n)
+    w = rng.uniform(0.5, 2.0, n).astype(np.float32)
+    x = rng.uniform(0.1, 1.0, n).astype(np.float32)
+    u = np.arange(n, dtype=np.uint32)
+    z = np.zeros(n, dtype=np.uint32)
+    g = synth.GraphArrays(n, 1, 1, u, z, w, u, z, x)
+    og = oracle.OracleGraph.from_arrays(g)
+    wd, xd = w.astype(np.float64), x.astype(np.float64)
+    mu = (1 - BETA) * wd / wd.sum() + BETA * xd / xd.sum()
+    T = math.ceil(math.log(100 * n) / math.log(1 / (1 - ALPHA)))
+    tail = (1 - ALPHA) ** T
+    want_piT = ALPHA + n * mu * ((1 - ALPHA) - tail)
+    lam, piT = og.lambda_estimate(ALPHA, BETA)
+    np.testing.assert_allclose(piT, want_piT, rtol=1e-12)
+    assert lam == pytest.approx(want_piT.max() + n * tail, rel=1e-12)
+    _, _, P = oracle.dense_matrices_of(g, BETA)
+    np.testing.assert_allclose(P, np.tile(mu, (n, 1)), rtol=1e-12)
+    colsum = oracle.pi_matrix(P, ALPHA).sum(axis=0)
+    np.testing.assert_allclose(colsum, ALPHA + (1 - ALPHA) * n * mu, rtol=1e-10)
+    assert lam >= colsum.max()
+
+
 def test_lemma3_invariant_every_round(tiny):
     """Lemma 3: pi(q, .) = pi_hat + r Pi after every round (APP and ASRP)."""
     og, Pi, q, lam = tiny["og"], tiny["Pi"], tiny["q"], tiny["lam"]
