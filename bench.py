@@ -138,6 +138,7 @@ def cpu_oracle_sample(g, eps, n_queries, seed=11):
         "value": n_queries / wall,
         "unit": "queries/s",
         "cores": n_queries,
+        "cpu_model": host_cpu_model(),
         "kind": "oracle",
         "sample": (f"{n_queries} ASRP queries (FP64, single-threaded each, one process per core) "
                    f"on the same graph; wall {wall:.1f} s; per-query p50 "
@@ -156,6 +157,25 @@ def host_cores():
         return len(os.sched_getaffinity(0))
     except Exception:
         return os.cpu_count() or 1
+
+
+def host_cpu_model():
+    """The host CPU's model name (lscpu, else /proc/cpuinfo), or None."""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.lower().startswith("model name"):
+                return line.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    try:
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                if line.lower().startswith("model name"):
+                    return line.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    return None
 
 
 # ------------------------------------------------------------------- clocks
@@ -516,7 +536,7 @@ def run_ours(args, rank, world, local_rank):
         "roofline": roof,
         "parity": parity,
         "ablation": ablation,
-        "cpu_baseline": cpu and {k: cpu[k] for k in ("value", "unit", "cores", "kind", "sample")},
+        "cpu_baseline": cpu and {k: cpu[k] for k in ("value", "unit", "cores", "cpu_model", "kind", "sample")},
         "e2e": e2e,
         "gpu_launches": K,
         "clocks": clocks,
@@ -773,7 +793,8 @@ def run_reference(args, rank, world):
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic", "impl": "reference",
         "config": workload_config(args, {"reference": "FP64 CPU oracle (the paper ships no code)"}),
-        "cpu_baseline": {"value": value, "unit": "queries/s", "cores": n, "kind": "oracle",
+        "cpu_baseline": {"value": value, "unit": "queries/s", "cores": n, "cpu_model": host_cpu_model(),
+                         "kind": "oracle",
                          "sample": f"{n} queries per step, one process per core, lambda {lam:.2f}"},
         "e2e": {"value": value, "unit": "queries/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
