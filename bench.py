@@ -282,21 +282,52 @@ NCU_TRAFFIC = {
     "bytes_per_tile_round": 257.40e9 / 106,
     # l1tex__m_xbar2l1tex_read_bytes.sum of the same capture: bytes moved from L2 to the SMs
     "l2_to_sm_bytes_per_tile_round": 944.894883e9 / 106,
-    "sources": {"ahpp_batch.cu": "de4b77bce76bf143", "ahpp_batch.cuh": "f3dfbbd4287bd668",
-                "ahpp_internal.cuh": "b85a585f011dc3c6"},
+    # code_digest of the kernel sources at capture (raw sha256 prefixes then:
+    # ahpp_batch.cu de4b77bce76bf143, ahpp_batch.cuh f3dfbbd4287bd668,
+    # ahpp_internal.cuh b85a585f011dc3c6)
+    "sources": {"ahpp_batch.cu": "f93e83d641d310da", "ahpp_batch.cuh": "88a9e3865a4bf806",
+                "ahpp_internal.cuh": "aa651509cd78fba7"},
 }
+
+
+def code_digest(text):
+    """sha256 prefix of C/C++/CUDA source with its comments removed and every
+    run of whitespace made one space: the same for two versions of a file
+    that differ only in comments or layout, different when the code differs."""
+    import hashlib
+    out, i, n = [], 0, len(text)
+    while i < n:
+        c = text[i]
+        if c in "\"'":                                  # string or character literal
+            j = i + 1
+            while j < n and text[j] != c:
+                j += 2 if text[j] == "\\" else 1
+            out.append(text[i:j + 1])
+            i = j + 1
+        elif text.startswith("//", i):
+            j = text.find("\n", i)
+            i = n if j < 0 else j
+        elif text.startswith("/*", i):
+            j = text.find("*/", i + 2)
+            out.append(" ")
+            i = n if j < 0 else j + 2
+        else:
+            out.append(c)
+            i += 1
+    code = " ".join("".join(out).split())
+    return hashlib.sha256(code.encode()).hexdigest()[:16]
 
 
 def ncu_traffic(graph, tile_rounds, key="bytes_per_tile_round"):
     """Bytes of one launch scaled from the capture (DRAM by default, or the
-    L2 -> SM bytes), or None if it does not describe the kernel as built now."""
-    import hashlib
+    L2 -> SM bytes), or None if it does not describe the kernel as built now
+    (the code of a source file, comments aside, differs from the captured)."""
     if graph != NCU_TRAFFIC["graph"]:
         return None
     csrc = os.path.join(ROOT, "paper_2512_11606_gb300", "csrc")
     for name, want in NCU_TRAFFIC["sources"].items():
-        with open(os.path.join(csrc, name), "rb") as f:
-            if hashlib.sha256(f.read()).hexdigest()[:16] != want:
+        with open(os.path.join(csrc, name), encoding="utf-8") as f:
+            if code_digest(f.read()) != want:
                 return None
     return NCU_TRAFFIC[key] * tile_rounds
 

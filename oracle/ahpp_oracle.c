@@ -284,7 +284,7 @@ typedef struct {              /* per-round record, arrays of length cap */
     uint8_t *phase;           /* 0 async / 1 sync */
 } og_trace;
 
-/* One round of Algorithm 3 (lines 4-19).  The selected set is fixed at the
+/* One round of Algorithm 3 (U-push, then the V and attribute flushes).  The selected set is fixed at the
  * start of the round: node u is pushed iff r_u[u] > th_scale * th_u[u]
  * (th_u == NULL: iff r_u[u] > th_scale).  Returns |F_U|. */
 static uint64_t og_round(const og_graph *g, double alpha, double beta,
@@ -296,7 +296,7 @@ static uint64_t og_round(const og_graph *g, double alpha, double beta,
         double th = th_u ? th_scale * (double)th_u[u] : th_scale;
         if (r_u[u] > th) sel[nf++] = u;
     }
-    for (uint64_t i = 0; i < nf; i++) {          /* lines 4-11 */
+    for (uint64_t i = 0; i < nf; i++) {          /* push each selected U node */
         uint32_t u = sel[i];
         double r = r_u[u];
         pi[u] += alpha * r;
@@ -312,14 +312,14 @@ static uint64_t og_round(const og_graph *g, double alpha, double beta,
         r_u[u] = 0.0;
         *n_p += nv + na;
     }
-    for (uint32_t v = 0; v < g->n_v; v++) {      /* lines 12-15 */
+    for (uint32_t v = 0; v < g->n_v; v++) {      /* flush every V residue to U */
         if (!(r_v[v] > 0.0)) continue;
         for (uint64_t k = g->vu.off[v]; k < g->vu.off[v + 1]; k++)
             r_u[g->vu.col[k]] += g->vu.w[k] / g->d_v[v] * r_v[v];
         *n_p += g->vu.off[v + 1] - g->vu.off[v];
         r_v[v] = 0.0;
     }
-    for (uint32_t a = 0; a < g->n_a; a++) {      /* lines 16-19 */
+    for (uint32_t a = 0; a < g->n_a; a++) {      /* flush every attribute residue to U */
         if (!(r_a[a] > 0.0)) continue;
         for (uint64_t k = g->au.off[a]; k < g->au.off[a + 1]; k++)
             r_u[g->au.col[k]] += g->au.w[k] / g->wcol_a[a] * r_a[a];
@@ -368,7 +368,7 @@ int og_push(const og_graph *g, int algo, double alpha, double beta, uint32_t q,
     memset(st, 0, sizeof(*st));
     for (uint32_t u = 0; u < n; u++)
         cnt[u] = (uint32_t)((g->uv.off[u + 1] - g->uv.off[u]) + (g->ua.off[u + 1] - g->ua.off[u]));
-    r_u[q] = 1.0;                                   /* lines 1-2 */
+    r_u[q] = 1.0;                                   /* unit residue at the source */
     double EE = (double)(g->uv.nnz + g->ua.nnz);
     double r_max = eps / EE;                        /* APP threshold scale */
     double eps_f = (algo == OG_ASRP) ? eps / lambda : 0.0;
@@ -379,7 +379,7 @@ int og_push(const og_graph *g, int algo, double alpha, double beta, uint32_t q,
     int rc = OG_OK;
     uint32_t round = 0;
     for (;;) {
-        /* loop test (Algorithm 3 line 3; Algorithm 4 lines 5 and 27) */
+        /* loop test of Algorithms 3 and 4: some U residue above its threshold */
         int any = 0;
         for (uint32_t u = 0; u < n && !any; u++) {
             double th = (algo == OG_APP) ? r_max * (double)cnt[u] : eps_f;
@@ -405,7 +405,7 @@ int og_push(const og_graph *g, int algo, double alpha, double beta, uint32_t q,
             tr->sum_pi[round - 1] = p;
             tr->phase[round - 1] = (uint8_t)sync;
         }
-        if (algo == OG_ASRP && !sync) {             /* lines 25-26 */
+        if (algo == OG_ASRP && !sync) {             /* ASRP's switch test */
             double budget;
             if (switch_rule == 1)
                 budget = 2.0 * EE * (log(1.0 / (lambda * m)) / lg);
@@ -459,12 +459,12 @@ int og_forward_push(const og_graph *g, double alpha, double beta, uint32_t q, do
         if (st->pushes >= max_pushes) { rc = OG_ENOTCONVERGED; break; }
         st->pushes++;
         double ru = r[u];
-        pi[u] += alpha * ru;                         /* line 4 */
-        double rho = (1.0 - alpha) * ru;            /* line 5 */
-        r[u] = 0.0;                                  /* line 6 */
+        pi[u] += alpha * ru;                         /* reserve */
+        double rho = (1.0 - alpha) * ru;            /* mass to spread */
+        r[u] = 0.0;                                  /* residue consumed */
         if (g->uv.off[u + 1] == g->uv.off[u]) leak += (1.0 - beta) * rho;
         if (g->ua.off[u + 1] == g->ua.off[u]) leak += beta * rho;
-        for (uint64_t k = g->uv.off[u]; k < g->uv.off[u + 1]; k++) {   /* lines 7-9 */
+        for (uint64_t k = g->uv.off[u]; k < g->uv.off[u + 1]; k++) {   /* via V: (1-beta) share */
             uint32_t v = g->uv.col[k];
             double c = (1.0 - beta) * g->uv.w[k] / g->d_u[u] / g->d_v[v] * rho;
             for (uint64_t j = g->vu.off[v]; j < g->vu.off[v + 1]; j++) {
@@ -473,7 +473,7 @@ int og_forward_push(const og_graph *g, double alpha, double beta, uint32_t q, do
                 if (!inq[x] && r[x] > r_max * cnt[x]) { queue[tail++ % cap] = x; inq[x] = 1; }
             }
         }
-        for (uint64_t k = g->ua.off[u]; k < g->ua.off[u + 1]; k++) {   /* lines 10-12 */
+        for (uint64_t k = g->ua.off[u]; k < g->ua.off[u + 1]; k++) {   /* via A: beta share */
             uint32_t a = g->ua.col[k];
             double c = beta * g->ua.w[k] / g->wrow_u[u] / g->wcol_a[a] * rho;
             for (uint64_t j = g->au.off[a]; j < g->au.off[a + 1]; j++) {

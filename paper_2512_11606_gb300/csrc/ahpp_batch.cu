@@ -833,7 +833,7 @@ k_tiles(const __grid_constant__ DevGraph g, const __grid_constant__ BatchState s
     const uint32_t qi = tile * kTile + lane;            // query (batch) or slot (serve) index
     uint32_t tround = SERVE ? sv.tile_round[tile] : 0u;
 
-    // ---- admission: Algorithm 3 lines 1-2 for every new lane
+    // ---- admission: the initial state of Algorithm 3 (unit residue at the source) for every new lane
     if (!SERVE) {
       for (size_t i = c.gt; i < nu32; i += c.nt) { tb.r_u[i] = 0.f; tb.pi[i] = 0.f; tb.pic[i] = 0.f; }
       for (size_t i = c.gt; i < (size_t)g.n_v * kTile; i += c.nt) tb.t_v[i] = 0.f;

@@ -3,8 +3,8 @@
 //
 // A round is either
 //   * a push round (small frontier): U-push of the marked list with atomic
-//     scatter into t_V / t_A (Algorithm 3 lines 4-11), then the flush of every
-//     touched V node and attribute (lines 12-19) with atomic scatter into
+//     scatter into t_V / t_A (the U-push of Algorithm 3), then the flush of
+//     every touched V node and attribute (its V and attribute steps) into
 //     r_U, then the selection of the next frontier (warp-ballot compaction);
 //   * a pull round (large frontier, the synchronous sweep of Algorithm 4):
 //     phase 1 gathers t_V / t_A from the marked residues over V->U and A->U
@@ -343,7 +343,7 @@ k_query1(const __grid_constant__ DevGraph g, const __grid_constant__ Q1State s,
   const unsigned int nb = gridDim.x;
   const bool app = p.algo == kAlgoAPP;
 
-  // ---- init: zero the state, mark the source (Algorithm 3 lines 1-2)
+  // ---- init: zero the state, mark the source (the initial state of Algorithm 3)
   const float r0 = p.lambda_mode ? -1.f : 0.f;
   for (uint32_t u = c.gt; u < g.n_u; u += c.nt) { s.r_u[u] = r0; s.pi[u] = 0.f; s.pic[u] = 0.f; }
   for (uint32_t v = c.gt; v < g.n_v; v += c.nt) s.t_v[v] = 0.f;

@@ -107,3 +107,12 @@ def test_steady_state_counts_whole_bursts():
     # without the snapping, window edges inside bursts read off the rate
     lo, hi = 40, len(done_t) - 40
     assert abs((hi - lo) / (done_t[hi - 1] - done_t[lo - 1]) / (burst / period) - 1) > 0.005
+
+
+def test_code_digest_ignores_comments_and_layout_only():
+    src = 'int f(int x) {  // add one\n  /* body */ return x + 1;\n}\nconst char* s = "a // b";\n'
+    same = 'int f(int x) { /* a different comment */\n\n    return x + 1; }\nconst char* s = "a // b"; // c\n'
+    assert bench.code_digest(src) == bench.code_digest(same)
+    assert bench.code_digest(src) != bench.code_digest(src.replace("x + 1", "x + 2"))
+    assert bench.code_digest(src) != bench.code_digest(src.replace('"a // b"', '"a /* b"'))
+    assert bench.code_digest("char c = '\\'';") != bench.code_digest("char c = '\\\\';")
