@@ -473,6 +473,22 @@ def test_asrp_selection_rule_of_each_phase(tiny):
     assert wider
 
 
+def test_asrp_topk_precision_against_exact(tiny):
+    """The measure of Fig. 7: the top-k of ASRP at eps = 1e-6 against the
+    top-k of exact AHPP (a row of the dense Pi), nodes within 2 eps of the
+    exact k-th score counted as interchangeable (ties, C-8)."""
+    og, Pi, lam = tiny["og"], tiny["Pi"], tiny["lam"]
+    eps = 1e-6
+    for q in synth.draw_queries(og.n_u, 3, seed=7):
+        exact = Pi[int(q)]
+        res = og.push("asrp", ALPHA, BETA, int(q), eps, lam=lam)
+        for k in (10, 50, 100):
+            kth = np.sort(exact)[::-1][k - 1]
+            ok = set(np.where(exact >= kth - 2 * eps)[0].tolist())
+            got = oracle.topk(res.pi, k)[0].tolist()
+            assert len(set(got) & ok) / k >= 0.99, (int(q), k)
+
+
 def test_topk_matches_sorting(tiny):
     rng = np.random.default_rng(3)
     s = np.round(rng.random(500), 2)            # many ties
