@@ -231,7 +231,8 @@ int ahpp_query_batch_device(ahpp_graph *g, uint32_t n, const uint32_t *d_q, cons
  * serialised because they share the array (overlapping use would race).  The
  * first call on a device resolves the array's address with that device
  * current: make it before any stream capture.  Returns AHPP_OK,
- * AHPP_ENOTCONVERGED, AHPP_EINVAL or AHPP_ECUDA. */
+ * AHPP_ENOTCONVERGED, AHPP_EINVAL, AHPP_ETIMEOUT (a device wait gave up) or
+ * AHPP_ECUDA. */
 int ahpp_query_dense_noalloc(ahpp_graph *g, uint32_t q, double eps, float *d_out_pi, void *stream);
 
 /* Device-resident single query (the plain path) on stream (NULL = graph's):
@@ -307,6 +308,18 @@ int ahpp_row_access_peak(int device, uint64_t table_bytes, int op, double *rows_
  * whether a kernel launched afterwards ran (1 expected).  Takes a few
  * seconds.  AHPP_EINVAL for bad arguments, AHPP_ECUDA if a CUDA call fails. */
 int ahpp_selftest_wait_timeout(int device, int *blocks_gave_up, int *context_ok);
+
+/* Self-test of the same detection inside the query kernels (no fault, no
+ * hang: every wait is bounded).  Arms a one-shot trap on g: the next
+ * persistent launch made through g (ahpp_query / ahpp_query_dense /
+ * ahpp_query_device, the batched entry points, ahpp_query_dense_noalloc,
+ * ahpp_power_iteration, or a serving step) clears its grid barrier with a
+ * counter that can never reach the block count, so the launch's first wait,
+ * before any push round, gives up after about a second.  That call must then
+ * report AHPP_ETIMEOUT (batched: stats status 2 for every query; serving:
+ * the server fails every request with AHPP_ETIMEOUT and stops), and the
+ * graph stays usable for the next call.  AHPP_EINVAL for a NULL g. */
+int ahpp_selftest_arm_wait_timeout(ahpp_graph *g);
 
 #ifdef __cplusplus
 }

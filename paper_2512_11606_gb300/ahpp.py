@@ -120,6 +120,7 @@ SIGNATURES = {
                                             ctypes.POINTER(ctypes.c_double)]),
     "ahpp_selftest_wait_timeout": (ctypes.c_int, [ctypes.c_int, ctypes.POINTER(ctypes.c_int),
                                                   ctypes.POINTER(ctypes.c_int)]),
+    "ahpp_selftest_arm_wait_timeout": (ctypes.c_int, [_vp]),
 }
 
 
@@ -320,6 +321,12 @@ class Graph:
         return _check(lib().ahpp_query_dense_noalloc(
             self._h, q, eps, out_t.data_ptr(), None if stream is None else stream.cuda_stream),
             (AHPP_ENOTCONVERGED,))
+
+    def arm_wait_timeout(self) -> None:
+        """Self-test: the next persistent launch on this graph starts with a
+        grid barrier that can never fill, so its call reports AHPP_ETIMEOUT
+        after about a second (ahpp_selftest_arm_wait_timeout)."""
+        _check(lib().ahpp_selftest_arm_wait_timeout(self._h))
 
     def autotune(self, q_sample, eps: float) -> dict:
         q = np.ascontiguousarray(q_sample, np.uint32)

@@ -31,13 +31,13 @@ __global__ void k_scatter_dense(const float* __restrict__ pi, const uint32_t* __
     out[n2o[u]] = pi[u];
 }
 
-__global__ void k_ctl_to_stats(const QCtl* ctl, const unsigned int* maxr, double lambda,
-                               double eps_f, ahpp_stats* st) {
+__global__ void k_ctl_to_stats(const QCtl* ctl, const unsigned int* maxr, const GridBarrier* bar,
+                               double lambda, double eps_f, ahpp_stats* st) {
   ahpp_stats S;
   S.rounds = ctl->rounds;
   S.switch_round = ctl->switch_round;
   S.dense_rounds = ctl->dense_rounds;
-  S.status = (uint32_t)ctl->status;
+  S.status = bar->err ? (uint32_t)kStatusWait : (uint32_t)ctl->status;
   S.pushes = ctl->pushes;
   S.n_p = ctl->n_p;
   S.resid_sum = ctl->resid_sum;
@@ -48,6 +48,21 @@ __global__ void k_ctl_to_stats(const QCtl* ctl, const unsigned int* maxr, double
   S.eps_f = eps_f;
   S.served_ms = 0.0;
   *st = S;
+}
+
+struct WaitBars {
+  const GridBarrier* bar[kMaxGroups];
+  uint32_t n_bars;
+};
+
+__global__ void k_batch_wait_status(const WaitBars wb, uint32_t n, ahpp_stats* st, uint32_t* out_n) {
+  unsigned int err = 0;
+  for (uint32_t i = 0; i < wb.n_bars; ++i) err |= wb.bar[i]->err;
+  if (!err) return;
+  for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    if (st) st[i].status = kStatusWait;
+    if (out_n) out_n[i] = 0;
+  }
 }
 
 int status_code(int status) {
@@ -104,9 +119,27 @@ Q1Params noalloc_params(const ahpp_graph* g, uint32_t q_new, double eps) {
   return q1_params(g, q_new, eps);
 }
 
+int reset_barrier(ahpp_graph* g, GridBarrier* bar, cudaStream_t stream, bool keep_trap) {
+  AHPP_CUDA(cudaMemsetAsync(bar, 0, sizeof(GridBarrier), stream));
+  if (g && g->wait_trap.load()) {
+    // 0x40404040 arrivals: the block count is never reached
+    AHPP_CUDA(cudaMemsetAsync(&bar->count, 0x40, sizeof(bar->count), stream));
+    if (!keep_trap) g->wait_trap.store(0);
+  }
+  return AHPP_OK;
+}
+
+int barrier_status(GridBarrier* bar, cudaStream_t stream, int* status) {
+  unsigned int err = 0;
+  AHPP_CUDA(cudaMemcpyAsync(&err, &bar->err, sizeof(err), cudaMemcpyDeviceToHost, stream));
+  AHPP_CUDA(cudaStreamSynchronize(stream));
+  *status = err ? kStatusWait : kStatusOk;
+  return AHPP_OK;
+}
+
 int run_query1_launch(ahpp_graph* g, uint32_t q_new, double eps, cudaStream_t stream) {
   Q1Params p = q1_params(g, q_new, eps);
-  AHPP_CUDA(cudaMemsetAsync(g->q1.bar, 0, sizeof(GridBarrier), stream));
+  if (int rc = reset_barrier(g, g->q1.bar, stream)) return rc;
   int e = launch_query1(g->dg, g->q1, p, g->bf16, g->q1_grid, stream);
   if (e) return cuda_fail((cudaError_t)e, "k_query1 launch");
   return AHPP_OK;
@@ -125,15 +158,19 @@ int run_lambda(ahpp_graph* g) {
   p.kahan = 1;
   p.max_rounds = T;
   p.trace_cap = 0;
-  AHPP_CUDA(cudaMemsetAsync(g->q1.bar, 0, sizeof(GridBarrier), g->stream));
+  if (int rc = reset_barrier(nullptr, g->q1.bar, g->stream)) return rc;
   int e = launch_query1(g->dg, g->q1, p, g->bf16, g->q1_grid, g->stream);
   if (e) return cuda_fail((cudaError_t)e, "lambda launch");
   unsigned int bits[2] = {0, 0};
   QCtl ctl;
   AHPP_CUDA(cudaMemcpyAsync(bits, g->q1.final_maxr_bits, sizeof(bits), cudaMemcpyDeviceToHost, g->stream));
   AHPP_CUDA(cudaMemcpyAsync(&ctl, g->q1.ctl, sizeof(ctl), cudaMemcpyDeviceToHost, g->stream));
-  AHPP_CUDA(cudaStreamSynchronize(g->stream));
-  if (ctl.status == kStatusWait) { set_error("lambda estimate: device wait gave up"); return AHPP_ETIMEOUT; }
+  int bst = kStatusOk;
+  if (int rc = barrier_status(g->q1.bar, g->stream, &bst)) return rc;
+  if (ctl.status == kStatusWait || bst == kStatusWait) {
+    set_error("lambda estimate: device wait gave up");
+    return AHPP_ETIMEOUT;
+  }
   float maxpi;
   std::memcpy(&maxpi, &bits[1], 4);
   // FP32 rounding of pi_T is covered by a 1e-4 relative margin; the tail
@@ -147,8 +184,7 @@ int ensure_batch(ahpp_graph* g, uint32_t groups, uint32_t kmax) {
   kmax = std::max<uint32_t>(kmax, 1);
   if (s.n_groups >= groups && s.kmax_cap >= kmax) return AHPP_OK;
   const DevGraph& G = g->dg;
-  const size_t n_split = std::max((size_t)G.b_v.n_split + G.b_a.n_split + G.b_u.n_split,
-                                  (size_t)G.m_v.n_split + G.m_a.n_split + G.m_u.n_split);
+  const size_t n_split = (size_t)G.b_v.n_split + G.b_a.n_split + G.b_u.n_split;
   const uint32_t kcap = std::max(kmax, s.kmax_cap);
   const uint32_t ng = std::max(groups, s.n_groups);
   uint64_t bytes = 0;
@@ -175,10 +211,6 @@ int ensure_batch(ahpp_graph* g, uint32_t groups, uint32_t kmax) {
         return AHPP_ENOMEM;
       }
       AHPP_CUDA(cudaMemset(t.bar, 0, sizeof(GridBarrier)));
-      if (encode_tile_maps(t, G.n_u, G.n_v, G.n_a) != 0) {
-        set_error("batched state: tensor map encoding failed");
-        return AHPP_ECUDA;
-      }
     }
     if (fresh || kcap > s.kmax_cap) {
       t.cand = (unsigned long long*)A((size_t)kTile * kcap * 8);
@@ -227,9 +259,17 @@ int run_batch_launch(ahpp_graph* g, uint32_t n, const uint32_t* d_q, const doubl
                                    : auto_rounds(1e-14 / std::max(g->lambda, 1.0), g->cfg.alpha);
   p.groups = groups;
   for (uint32_t i = 0; i < groups; ++i)
-    AHPP_CUDA(cudaMemsetAsync(g->bt.tb[i].bar, 0, sizeof(GridBarrier), stream));
+    if (int rc = reset_barrier(g, g->bt.tb[i].bar, stream, i + 1 < groups)) return rc;
   int e = launch_batch(g->dg, g->bt, p, g->bf16, grid, stream);
   if (e) return cuda_fail((cudaError_t)e, "k_batch launch");
+  // a group whose barrier gave up may have left some of its tiles without
+  // results: report every query of the launch as a device wait that gave up
+  WaitBars wb{};
+  for (uint32_t i = 0; i < groups; ++i) wb.bar[i] = g->bt.tb[i].bar;
+  wb.n_bars = groups;
+  k_batch_wait_status<<<std::max<uint32_t>(1, std::min<uint32_t>((n + 255) / 256, 1024)), 256, 0, stream>>>(
+      wb, n, d_stats, d_n);
+  AHPP_CUDA(cudaGetLastError());
   return AHPP_OK;
 }
 
@@ -246,7 +286,8 @@ int run_single_device(ahpp_graph* g, uint32_t q, double eps, uint32_t k, uint32_
     AHPP_CUDA(cudaMemsetAsync(d_out_n, 0, 4, s));
   }
   if (d_stats) {
-    k_ctl_to_stats<<<1, 1, 0, s>>>(g->q1.ctl, g->q1.final_maxr_bits, g->lambda, eps_f_of(g, eps), d_stats);
+    k_ctl_to_stats<<<1, 1, 0, s>>>(g->q1.ctl, g->q1.final_maxr_bits, g->q1.bar, g->lambda,
+                                   eps_f_of(g, eps), d_stats);
     AHPP_CUDA(cudaGetLastError());
   }
   return AHPP_OK;
@@ -421,7 +462,9 @@ static int finish_single(ahpp_graph* g, double eps, ahpp_stats* st) {
   unsigned int bits[2];
   AHPP_CUDA(cudaMemcpyAsync(&ctl, g->q1.ctl, sizeof(ctl), cudaMemcpyDeviceToHost, g->stream));
   AHPP_CUDA(cudaMemcpyAsync(bits, g->q1.final_maxr_bits, sizeof(bits), cudaMemcpyDeviceToHost, g->stream));
-  AHPP_CUDA(cudaStreamSynchronize(g->stream));
+  int bst = kStatusOk;
+  if (int rc = barrier_status(g->q1.bar, g->stream, &bst)) return rc;
+  if (bst == kStatusWait) ctl.status = kStatusWait;
   if (st) {
     st->rounds = ctl.rounds;
     st->switch_round = ctl.switch_round;
@@ -459,7 +502,7 @@ int ahpp_power_iteration(ahpp_graph* g, uint32_t q, uint32_t T, float* out_pi, a
   p.eps_f = 0.0;
   p.max_rounds = T;
   p.trace_cap = 0;
-  AHPP_CUDA(cudaMemsetAsync(g->q1.bar, 0, sizeof(GridBarrier), g->stream));
+  if (int rc = reset_barrier(g, g->q1.bar, g->stream)) return rc;
   int e = launch_query1(g->dg, g->q1, p, g->bf16, g->q1_grid, g->stream);
   if (e) return cuda_fail((cudaError_t)e, "power iteration launch");
   int rc;

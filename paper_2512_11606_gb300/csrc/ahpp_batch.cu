@@ -10,7 +10,6 @@
 // on the other queries of the tile.  Top-k per query is a per-lane radix
 // select over (score, caller id) keys.
 #include "ahpp_batch.cuh"
-#include "ahpp_tma.cuh"
 
 namespace ahpp {
 
@@ -73,18 +72,7 @@ constexpr int kQL = 4;                 // queries per lane
 constexpr int kGL = kTile / kQL;       // lanes per row group (one 128- or 64-byte line)
 constexpr int kGPW = 32 / kGL;         // row groups per warp
 static_assert(kTile == 16 || kTile == 32, "tile of 16 or 32 queries");
-#ifndef AHPP_ATTR_PUSH
-#define AHPP_ATTR_PUSH 1          // attribute hop pushed from phase 2 (1) or pulled in phase 1 (0); 1 measured faster
-#endif
-#ifndef AHPP_TMA
-#define AHPP_TMA 0                // 1: pull phases gather rows with TMA tile::gather4 (correct, measured 2.6x slower)
-#endif
-#ifndef AHPP_P1_PASSES
-#define AHPP_P1_PASSES 1          // 2: phase 1 gathers the two halves of U in separate passes (measured slower)
-#endif
-#ifndef AHPP_BATCH_MINB
-#define AHPP_BATCH_MINB (AHPP_TMA ? 2 : (AHPP_ATTR_PUSH ? 3 : 4))   // resident blocks per SM the register budget targets (measured best)
-#endif
+constexpr int kBatchMinBlocks = 3;     // resident blocks per SM the register budget targets (measured best)
 
 // Smallest float f with (r > th) <=> (r >= f) for every float r: the mark
 // test r > th of Algorithm 4 taken exactly against the FP64 threshold.
@@ -94,50 +82,15 @@ __device__ __forceinline__ float threshold_up(double th) {
   return f;
 }
 
-// Gathered state (r_U rows in phase 1, t_V / t_A rows in phase 2) is loaded
-// with the L2 evict-last policy so that the streamed graph arrays (loaded
-// evict-first) do not push it out of L2 during a phase.
-__device__ __forceinline__ uint64_t policy_keep() {
-  uint64_t pol;
-  asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(pol));
-  return pol;
-}
-#ifndef AHPP_GATHER_HINT
-#define AHPP_GATHER_HINT 0        // gathers load with the L2 evict-last policy (measured slower)
-#endif
-#ifndef AHPP_STREAM_HINT
-#define AHPP_STREAM_HINT 1        // graph arrays and reserves are streamed with evict-first loads
-#endif
+// Graph arrays, reserves and compensations are read once per round:
+// streamed with the evict-first policy so that they do not push the
+// gathered state rows out of L2.
 template <typename T>
 __device__ __forceinline__ T ld_stream(const T* p) {
-#if AHPP_STREAM_HINT
   return __ldcs(p);
-#else
-  return *p;
-#endif
 }
-#ifndef AHPP_STORE_HINT
-#define AHPP_STORE_HINT 0         // rows that the next phase gathers are stored evict-last
-#endif
-__device__ __forceinline__ float4 ld_keep4(const float* p, uint64_t pol) {
-#if AHPP_GATHER_HINT
-  float4 v;
-  asm volatile("ld.global.L2::cache_hint.v4.f32 {%0, %1, %2, %3}, [%4], %5;"
-               : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w) : "l"(p), "l"(pol));
-  return v;
-#else
-  return *reinterpret_cast<const float4*>(p);
-#endif
-}
-__device__ __forceinline__ void st_keep4(float* p, float4 v) {
-#if AHPP_STORE_HINT
-  const uint64_t pol = policy_keep();
-  asm volatile("st.global.L2::cache_hint.v4.f32 [%0], {%1, %2, %3, %4}, %5;"
-               :: "l"(p), "f"(v.x), "f"(v.y), "f"(v.z), "f"(v.w), "l"(pol) : "memory");
-#else
-  *reinterpret_cast<float4*>(p) = v;
-#endif
-}
+
+__device__ __forceinline__ float4 ld4(const float* p) { return *reinterpret_cast<const float4*>(p); }
 
 // out[0..3] += v as a reduction that returns nothing: an atomicAdd on a
 // float4 whose result is unused is still issued as a returning atomic, and
@@ -299,15 +252,13 @@ __device__ __forceinline__ Unit unit_of(const ItemList& L, uint32_t u, const uin
 // and clears ta_zero, the buffer the coming phase 2 pushes into.
 template <typename WA>
 __device__ __forceinline__ void gphase1(const BCtx& c, RAcc* A, bool do_v, bool do_a, float* ta_out,
-                                        const float* ta_scan, float* ta_zero, bool count,
-                                        int pass = 0, int npass = 1) {
+                                        const float* ta_scan, float* ta_zero, bool count) {
   const DevGraph& g = c.g;
   const uint32_t lane = c.lane, gl = lane & (kGL - 1), gi = lane / kGL;
   const unsigned gmask = ((1u << kGL) - 1u) << (gi * kGL);
   const float* __restrict__ r_u = c.t.r_u;
-  const uint64_t pol = policy_keep();
   auto gp = [&](uint32_t u) {
-    const float4 x = ld_keep4(r_u + (size_t)u * kTile + kQL * gl, pol);
+    const float4 x = ld4(r_u + (size_t)u * kTile + kQL * gl);
     return make_float4(fmaxf(-x.x, 0.f), fmaxf(-x.y, 0.f), fmaxf(-x.z, 0.f), fmaxf(-x.w, 0.f));
   };
   Q4Partials part;
@@ -333,13 +284,7 @@ __device__ __forceinline__ void gphase1(const BCtx& c, RAcc* A, bool do_v, bool 
     Unit un{0, 0, 0, 0xffffffffu};
     const uint32_t* off = is_a ? g.au_off : g.vu_off;
     if (ok) un = is_a ? unit_of(g.b_a, uix - nuv, g.au_off) : unit_of(g.b_v, uix, g.vu_off);
-    uint32_t b = ok ? off[un.row] + un.b : 0, e = ok ? off[un.row] + un.e : 0;
-    if (ok && npass == 2) {
-      // pass 0 gathers sources u < u_half, pass 1 the rest (entries sorted by u)
-      const uint32_t mid = is_a ? g.au_mid[un.row] : g.vu_mid[un.row];
-      if (pass == 0) e = max(b, min(e, mid));
-      else b = min(e, max(b, mid));
-    }
+    const uint32_t b = ok ? off[un.row] + un.b : 0, e = ok ? off[un.row] + un.e : 0;
     const uint32_t waves = warp_max_u32(is_a ? 0u : (e - b + kGL - 1) / kGL);
     // V rows and attribute rows in one warp: both gathers run, each group
     // keeps the one of its own kind (ranges are empty for the other)
@@ -358,17 +303,8 @@ __device__ __forceinline__ void gphase1(const BCtx& c, RAcc* A, bool do_v, bool 
       s = tot;
     }
     const uint32_t R = un.row;
-    float* out = is_a ? ta_out + (size_t)R * kTile + kQL * gl : c.t.t_v + (size_t)R * kTile + kQL * gl;
-    if (npass == 2 && pass == 0) {             // partial sum of the first half
-      *reinterpret_cast<float4*>(out) = s;
-      continue;
-    }
-    if (npass == 2) {
-      const float4 h = *reinterpret_cast<const float4*>(out);
-      s = make_float4(s.x + h.x, s.y + h.y, s.z + h.z, s.w + h.w);
-    }
     if (!is_a) {
-      st_keep4(c.t.t_v + (size_t)R * kTile + kQL * gl, s);
+      *reinterpret_cast<float4*>(c.t.t_v + (size_t)R * kTile + kQL * gl) = s;
       const uint32_t d = g.vu_off[R + 1] - g.vu_off[R];
       part.np[0] += s.x > 0.f ? d : 0; part.np[1] += s.y > 0.f ? d : 0;
       part.np[2] += s.z > 0.f ? d : 0; part.np[3] += s.w > 0.f ? d : 0;
@@ -428,7 +364,7 @@ __device__ __forceinline__ float4 gepilogue2(const BCtx& c, uint32_t u, float4 s
       rr[j] = r_new;
     }
   }
-  st_keep4(c.t.r_u + i, r);
+  *rp = r;
   if (pushed_any) { __stcs(pp, pv); __stcs(cp, pc); }
   return pushed;
 }
@@ -482,9 +418,8 @@ __device__ __forceinline__ void gphase2(const BCtx& c, const LaneCtl* ctl, RAcc*
   }
   const float* __restrict__ t_v = c.t.t_v;
   const float* __restrict__ t_a = ta_in;
-  const uint64_t pol = policy_keep();
-  auto gv = [&](uint32_t v) { return ld_keep4(t_v + (size_t)v * kTile + kQL * gl, pol); };
-  auto ga = [&](uint32_t a) { return ld_keep4(t_a + (size_t)a * kTile + kQL * gl, pol); };
+  auto gv = [&](uint32_t v) { return ld4(t_v + (size_t)v * kTile + kQL * gl); };
+  auto ga = [&](uint32_t a) { return ld4(t_a + (size_t)a * kTile + kQL * gl); };
   Q4Partials part;
   const uint32_t total = g.b_u.n_items + (g.n_u - g.b_u.n_long);
   for (uint32_t base = c.gw * kGPW; base < total; base += c.nw * kGPW) {
@@ -524,232 +459,6 @@ __device__ __forceinline__ void gphase2(const BCtx& c, const LaneCtl* ctl, RAcc*
   flush_q4(part, A);
 }
 
-// ------------------------------------------------------------------------
-// TMA form of the pull phases (one query per lane; kTile == 32).  A warp
-// owns an item (up to 32 consecutive rows, or one chunk of a long row) and
-// walks its neighbour entries in stages of 32 through a two-buffer gather
-// pipeline; row sums go to sp[row][lane] in shared memory.
-#if AHPP_TMA
-static_assert(kTile == 32, "the TMA phases map one query per lane");
-
-template <bool ADD, typename LoadF, typename XF>
-__device__ __forceinline__ void tma_rows(GatherPipe& gp, const CUtensorMap* map, uint32_t nrows,
-                                         uint32_t my_end, uint32_t kb, uint32_t ke, uint32_t lane,
-                                         LoadF load, XF xform, float* sp, unsigned int* err) {
-  if (!ADD)
-    for (uint32_t r = 0; r < nrows; ++r) sp[r * 32 + lane] = 0.f;
-  const uint32_t nst = (ke - kb + kStage - 1) / kStage;
-  uint32_t row = 0;
-  uint32_t row_end = __shfl_sync(kFull, my_end, 0);
-  float acc = 0.f;
-  if (nst == 0) return;
-  uint32_t idx = 0;
-  float coef = 0.f, coef_next = 0.f;
-  {
-    const uint32_t n0 = min((uint32_t)kStage, ke - kb);
-    if (lane < n0) load(kb + lane, idx, coef);
-    pipe_issue(gp, 0, map, lane < n0 ? idx : 0u, n0, lane);
-  }
-  for (uint32_t st = 0; st < nst; ++st) {
-    const int b = st & 1;
-    const uint32_t k0 = kb + st * kStage;
-    const uint32_t n = min((uint32_t)kStage, ke - k0);
-    if (st + 1 < nst) {
-      const uint32_t k1 = k0 + kStage;
-      const uint32_t n1 = min((uint32_t)kStage, ke - k1);
-      uint32_t i1 = 0;
-      coef_next = 0.f;
-      if (lane < n1) load(k1 + lane, i1, coef_next);
-      pipe_issue(gp, b ^ 1, map, lane < n1 ? i1 : 0u, n1, lane);
-    }
-    pipe_wait(gp, b, err);
-    const float* x = gp.buf + b * kStage * 32;
-    for (uint32_t j = 0; j < n; ++j) {
-      const float cj = __shfl_sync(kFull, coef, j);
-      while (k0 + j >= row_end) {
-        sp[row * 32 + lane] += acc;
-        acc = 0.f;
-        ++row;
-        row_end = __shfl_sync(kFull, my_end, row & 31u);
-      }
-      acc = fmaf(cj, xform(x[j * 32 + lane]), acc);
-    }
-    __syncwarp();
-    coef = coef_next;
-  }
-  if (row < nrows) sp[row * 32 + lane] += acc;
-}
-
-// Lane-scalar split-row combine (warp-collective): true for the chunk that
-// finishes the row, with the row total in *tot.
-__device__ __forceinline__ bool split_combine1(const TileBuf& t, uint32_t slot, uint32_t nch, float s,
-                                               uint32_t lane, float* tot) {
-  atomicAdd(&t.split_acc[(size_t)slot * kTile + lane], s);
-  __threadfence();
-  __syncwarp();
-  uint32_t last = 0;
-  if (lane == 0) last = atomicAdd(&t.split_cnt[slot], 1u) == nch - 1;
-  last = __shfl_sync(kFull, last, 0);
-  if (last) {
-    __threadfence();
-    *tot = atomicExch(&t.split_acc[(size_t)slot * kTile + lane], 0.f);
-    if (lane == 0) t.split_cnt[slot] = 0;
-  }
-  return last != 0;
-}
-
-// Item i of a TMA item list: rows [r0, r0 + nrows) whole, or one chunk.
-struct TItem {
-  uint32_t r0, nrows, z, w, slot;   // slot ~0: not split
-  bool chunk;
-};
-__device__ __forceinline__ TItem titem(const ItemList& L, uint32_t i) {
-  const uint4 it = L.items[i];
-  TItem t;
-  t.r0 = it.x;
-  t.chunk = (it.y & (kItemLong | kItemSplit)) != 0;
-  t.nrows = t.chunk ? 1u : it.y;
-  t.z = it.z; t.w = it.w;
-  t.slot = (it.y & kItemSplit) ? (it.y & kItemMask) : 0xffffffffu;
-  return t;
-}
-
-template <typename WA>
-__device__ __forceinline__ void tphase1(const BCtx& c, const TileBuf* tg, GatherPipe& gp, float* sp,
-                                        RAcc* A, unsigned int* err) {
-  const DevGraph& g = c.g;
-  const uint32_t lane = c.lane;
-  Partials part;
-  const uint32_t nv = g.m_v.n_items, total = nv + g.m_a.n_items;
-  auto neg = [](float x) { return fmaxf(-x, 0.f); };
-  for (uint32_t it = c.gw; it < total; it += c.nw) {
-    const bool is_a = it >= nv;
-    const TItem t = titem(is_a ? g.m_a : g.m_v, is_a ? it - nv : it);
-    const uint32_t* off = is_a ? g.au_off : g.vu_off;
-    uint32_t kb, ke, my_end;
-    if (t.chunk) {
-      kb = off[t.r0] + t.z; ke = off[t.r0] + t.w; my_end = ke;
-    } else {
-      kb = off[t.r0];
-      my_end = lane < t.nrows ? off[t.r0 + lane + 1] : 0xffffffffu;
-      ke = __shfl_sync(kFull, my_end, t.nrows - 1);
-    }
-    if (!is_a)
-      tma_rows<false>(gp, &tg->map_ru, t.nrows, my_end, kb, ke, lane,
-                      [&](uint32_t k, uint32_t& i, float& w) { i = ld_stream(g.vu_idx + k); w = ld_stream(g.vu_c + k); },
-                      neg, sp, err);
-    else
-      tma_rows<false>(gp, &tg->map_ru, t.nrows, my_end, kb, ke, lane,
-                      [&](uint32_t k, uint32_t& i, float& w) {
-                        i = ld_stream(g.au_idx + k);
-                        w = g.au_c[k];
-                      },
-                      neg, sp, err);
-    for (uint32_t row = 0; row < t.nrows; ++row) {
-      const uint32_t R = t.r0 + row;
-      float s = sp[row * 32 + lane];
-      if (t.slot != 0xffffffffu) {
-        const uint32_t slot = t.slot + (is_a ? g.m_v.n_split : 0);
-        const uint32_t nch = is_a ? g.m_a.split_nchunks[t.slot] : g.m_v.split_nchunks[t.slot];
-        float tot;
-        if (!split_combine1(c.t, slot, nch, s, lane, &tot)) continue;
-        s = tot;
-      }
-      if (!is_a) {
-        c.t.t_v[(size_t)R * kTile + lane] = s;
-        if (s > 0.f) part.np_flush += g.vu_off[R + 1] - g.vu_off[R];
-      } else {
-        const float tv = g.k_attr * g.cnorm_a[R] * s;
-        c.t.t_a[(size_t)R * kTile + lane] = tv;
-        if (tv > 0.f) part.np_flush += g.au_off[R + 1] - g.au_off[R];
-      }
-    }
-  }
-  flush_lane_partials(part, A);
-}
-
-// Residue update of row u for this lane's query (see gepilogue2).
-__device__ __forceinline__ void lepilogue2(const BCtx& c, uint32_t u, float s, uint32_t cnt, float th,
-                                           bool act, const LaneCtl* app_ctl, Partials& part) {
-  if (!act) return;
-  const size_t i = (size_t)u * kTile + c.lane;
-  const float r_old = c.t.r_u[i];
-  float kept = r_old;
-  if (r_old < 0.f) {
-    const float add = c.g.alpha * (-r_old);
-    if (c.p.kahan) {
-      float pv = ld_stream(c.t.pi + i), pc = ld_stream(c.t.pic + i);
-      kahan_add(pv, pc, add);
-      __stcs(c.t.pi + i, pv);
-      __stcs(c.t.pic + i, pc);
-    } else {
-      c.t.pi[i] += add;
-    }
-    kept = 0.f;
-  }
-  const float r_new = kept + s;
-  part.max_r = fmaxf(part.max_r, r_new);
-  const bool mark = app_ctl ? (double)r_new > app_ctl[c.lane].eps_f * (double)cnt : r_new >= th;
-  if (mark) {
-    c.t.r_u[i] = -r_new;
-    part.marked += 1;
-    part.marked_deg += cnt;
-  } else {
-    c.t.r_u[i] = r_new;
-  }
-}
-
-template <typename WA>
-__device__ __forceinline__ void tphase2(const BCtx& c, const TileBuf* tg, const LaneCtl* ctl,
-                                        GatherPipe& gp, float* sp, RAcc* A, unsigned int* err) {
-  const DevGraph& g = c.g;
-  const uint32_t lane = c.lane;
-  const bool app = c.p.algo == kAlgoAPP;
-  const LaneCtl& me = ctl[lane];
-  const bool act = me.active != 0;
-  const float th = app ? 0.f : threshold_up(me.phase == kPhaseSync ? 0.0 : me.eps_f);
-  auto id = [](float x) { return x; };
-  auto lv = [&](uint32_t k, uint32_t& i, float& w) { i = ld_stream(g.uv_idx + k); w = ld_stream(g.uv_w + k); };
-  auto la = [&](uint32_t k, uint32_t& i, float& w) { i = ld_stream(g.ua_idx + k); w = wload<WA>(g.ua_w, k); };
-  Partials part;
-  for (uint32_t it = c.gw; it < g.m_u.n_items; it += c.nw) {
-    const TItem t = titem(g.m_u, it);
-    if (t.chunk) {
-      const uint32_t u = t.r0;
-      const uint32_t b1 = g.uv_off[u], dv = g.uv_off[u + 1] - b1;
-      const uint32_t b2 = g.ua_off[u], da = g.ua_off[u + 1] - b2;
-      const uint32_t vb = b1 + min(t.z, dv), ve = b1 + min(t.w, dv);
-      const uint32_t ab = b2 + (t.z > dv ? t.z - dv : 0), ae = b2 + (t.w > dv ? t.w - dv : 0);
-      tma_rows<false>(gp, &tg->map_tv, 1, ve, vb, ve, lane, lv, id, sp, err);
-      tma_rows<true>(gp, &tg->map_ta, 1, ae, ab, ae, lane, la, id, sp, err);
-      float s = sp[lane];
-      if (t.slot != 0xffffffffu) {
-        const uint32_t sl = t.slot + g.m_v.n_split + g.m_a.n_split;
-        float tot;
-        if (!split_combine1(c.t, sl, g.m_u.split_nchunks[t.slot], s, lane, &tot)) continue;
-        s = tot;
-      }
-      lepilogue2(c, u, s, dv + da, th, act, app ? ctl : nullptr, part);
-    } else {
-      const uint32_t r0 = t.r0, nrows = t.nrows;
-      const uint32_t end_v = lane < nrows ? g.uv_off[r0 + lane + 1] : 0xffffffffu;
-      const uint32_t end_a = lane < nrows ? g.ua_off[r0 + lane + 1] : 0xffffffffu;
-      const uint32_t kv0 = g.uv_off[r0], ka0 = g.ua_off[r0];
-      const uint32_t kv1 = __shfl_sync(kFull, end_v, nrows - 1);
-      const uint32_t ka1 = __shfl_sync(kFull, end_a, nrows - 1);
-      tma_rows<false>(gp, &tg->map_tv, nrows, end_v, kv0, kv1, lane, lv, id, sp, err);
-      tma_rows<true>(gp, &tg->map_ta, nrows, end_a, ka0, ka1, lane, la, id, sp, err);
-      const uint32_t beg_v = __shfl_up_sync(kFull, end_v, 1), beg_a = __shfl_up_sync(kFull, end_a, 1);
-      const uint32_t my_cnt = lane < nrows ? (end_v - (lane ? beg_v : kv0)) + (end_a - (lane ? beg_a : ka0)) : 0u;
-      for (uint32_t row = 0; row < nrows; ++row) {
-        const uint32_t cnt = __shfl_sync(kFull, my_cnt, row);
-        lepilogue2(c, r0 + row, sp[row * 32 + lane], cnt, th, act, app ? ctl : nullptr, part);
-      }
-    }
-  }
-  flush_lane_partials(part, A);
-}
-#endif  // AHPP_TMA
 
 __device__ __forceinline__ double bbudget(const BatchParams& p, double eps_f, double M) {
   const double EE = (double)p.e_tot;
@@ -771,7 +480,7 @@ __device__ __forceinline__ unsigned long long score_key(float score, uint32_t ca
 // tiles already in flight, each live tile advances rounds_per_step rounds,
 // slots that finish are finalised and their top-k extracted).
 template <typename WA, bool SERVE>
-__global__ void __launch_bounds__(kThreads, AHPP_BATCH_MINB)
+__global__ void __launch_bounds__(kThreads, kBatchMinBlocks)
 k_tiles(const __grid_constant__ DevGraph g, const __grid_constant__ BatchState st,
         const __grid_constant__ BatchParams p, const __grid_constant__ ServeParams sv) {
   extern __shared__ __align__(1024) unsigned char smem[];
@@ -788,25 +497,6 @@ k_tiles(const __grid_constant__ DevGraph g, const __grid_constant__ BatchState s
   __shared__ uint32_t s_pick_cum[kTile], s_pick_h[kTile];
   __shared__ int s_flag;
   __shared__ TileBuf s_tb;
-#if AHPP_TMA
-  __shared__ __align__(8) uint64_t s_mbar[kWarps][2];
-  GatherPipe gp;
-  {
-    const uint32_t w = threadIdx.x >> 5;
-    gp.buf = reinterpret_cast<float*>(smem) + (size_t)w * (2 * kStage * 32 + 32 * 32);
-    gp.bar[0] = smem_u32(&s_mbar[w][0]);
-    gp.bar[1] = smem_u32(&s_mbar[w][1]);
-    gp.phase = 0;
-    if ((threadIdx.x & 31) == 0) {
-      mbar_init(gp.bar[0]);
-      mbar_init(gp.bar[1]);
-      mbar_fence_init();
-    }
-    __syncwarp();
-  }
-  float* const sp_tma = reinterpret_cast<float*>(smem) + (size_t)(threadIdx.x >> 5) * (2 * kStage * 32 + 32 * 32) +
-                        2 * kStage * 32;
-#endif
   const uint32_t groups = SERVE ? 1u : p.groups;
   const uint32_t nbg = gridDim.x / groups;              // blocks per group
   const uint32_t grp = blockIdx.x / nbg;
@@ -820,14 +510,13 @@ k_tiles(const __grid_constant__ DevGraph g, const __grid_constant__ BatchState s
   const bool warp0 = threadIdx.x < 32;
   const bool app = p.algo == kAlgoAPP;
   const uint32_t n_work = SERVE ? sv.n_live : (p.n + kTile - 1) / kTile;
-  const uint32_t n_split = max(g.b_v.n_split + g.b_a.n_split + g.b_u.n_split,
-                               g.m_v.n_split + g.m_a.n_split + g.m_u.n_split);
+  const uint32_t n_split = g.b_v.n_split + g.b_a.n_split + g.b_u.n_split;
   const size_t nu32 = (size_t)g.n_u * kTile;
   const uint32_t kmax = p.kmax;
 
   for (uint32_t w = grp; w < n_work; w += groups) {
     const uint32_t tile = SERVE ? sv.live[w] : w;
-    const TileBuf* tg = SERVE ? &sv.tbufs[tile] : &st.tb[grp];   // tensor maps live here
+    const TileBuf* tg = SERVE ? &sv.tbufs[tile] : &st.tb[grp];
     if (threadIdx.x == 0) s_tb = *tg;
     __syncthreads();
     const uint32_t qi = tile * kTile + lane;            // query (batch) or slot (serve) index
@@ -902,7 +591,7 @@ k_tiles(const __grid_constant__ DevGraph g, const __grid_constant__ BatchState s
         a0->marked_deg = cnt;
         // the source's attribute push of the first round (see push_attr)
         float* ta_cur = (tround & 1) ? tb.t_a2 : tb.t_a;
-        for (uint32_t k = g.ua_off[q_new]; AHPP_ATTR_PUSH && k < g.ua_off[q_new + 1]; ++k)
+        for (uint32_t k = g.ua_off[q_new]; k < g.ua_off[q_new + 1]; ++k)
           ta_cur[(size_t)g.ua_idx[k] * kTile + lane] += g.ua_pc[k];
       } else {
         tb.r_u[(size_t)q_new * kTile + lane] = 1.f;
@@ -937,26 +626,11 @@ k_tiles(const __grid_constant__ DevGraph g, const __grid_constant__ BatchState s
 
       float* ta_cur = (tround & 1) ? tb.t_a2 : tb.t_a;     // t_A of this round
       float* ta_next = (tround & 1) ? tb.t_a : tb.t_a2;    // t_A of the next round
-#if AHPP_TMA
-      tphase1<WA>(c, tg, gp, sp_tma, A, &tb.bar->err);
+      gphase1<WA>(c, A, true, false, nullptr, ta_cur, ta_next, true);
       if (!grid_sync(tb.bar, nbg)) { wait_fail = true; break; }
-      tphase2<WA>(c, tg, s_ctl, gp, sp_tma, A, &tb.bar->err);
-      if (!grid_sync(tb.bar, nbg)) { wait_fail = true; break; }
-      ++tround;
-#else
-      if (AHPP_P1_PASSES == 2) {
-        gphase1<WA>(c, A, true, !AHPP_ATTR_PUSH, ta_cur, nullptr, nullptr, false, 0, 2);
-        if (!grid_sync(tb.bar, nbg)) { wait_fail = true; break; }
-      }
-      if (AHPP_ATTR_PUSH)
-        gphase1<WA>(c, A, true, false, nullptr, ta_cur, ta_next, true, AHPP_P1_PASSES - 1, AHPP_P1_PASSES);
-      else
-        gphase1<WA>(c, A, true, true, ta_cur, nullptr, nullptr, true, AHPP_P1_PASSES - 1, AHPP_P1_PASSES);
-      if (!grid_sync(tb.bar, nbg)) { wait_fail = true; break; }
-      gphase2<WA>(c, s_ctl, A, ta_cur, AHPP_ATTR_PUSH ? ta_next : nullptr);
+      gphase2<WA>(c, s_ctl, A, ta_cur, ta_next);
       if (!grid_sync(tb.bar, nbg)) { wait_fail = true; break; }
       ++tround;
-#endif
 
       if (warp0) {
         LaneCtl L{};
@@ -1002,10 +676,8 @@ k_tiles(const __grid_constant__ DevGraph g, const __grid_constant__ BatchState s
         if (!grid_sync(tb.bar, nbg)) { wait_fail = true; break; }
         // the new marks also push into the next round's t_A: recompute it by
         // the pull form from the complete marks (once per switch)
-        if (AHPP_ATTR_PUSH) {
-          gphase1<WA>(c, A, false, true, (tround & 1) ? tb.t_a2 : tb.t_a, nullptr, nullptr, false);
-          if (!grid_sync(tb.bar, nbg)) { wait_fail = true; break; }
-        }
+        gphase1<WA>(c, A, false, true, (tround & 1) ? tb.t_a2 : tb.t_a, nullptr, nullptr, false);
+        if (!grid_sync(tb.bar, nbg)) { wait_fail = true; break; }
       }
     }
     if (wait_fail && warp0 && lq && s_ctl[lane].valid) {
@@ -1201,10 +873,8 @@ template __global__ void k_tiles<__nv_bfloat16, true>(const __grid_constant__ De
                                                       const __grid_constant__ BatchParams,
                                                       const __grid_constant__ ServeParams);
 
-// radix histograms / sort buffer (4096 keys); with TMA also the per-warp
-// gather stages (2 x 32 rows) and row sums (32 rows) of every warp
-constexpr size_t kBatchSmem = AHPP_TMA ? std::max<size_t>(32 * 1024, kWarps * (2 * kStage * 32 + 32 * 32) * 4)
-                                       : 32 * 1024;
+// radix histograms / sort buffer (4096 keys)
+constexpr size_t kBatchSmem = 32 * 1024;
 
 namespace {
 const void* tiles_fn(bool bf16, bool serve) {
@@ -1220,37 +890,6 @@ const void* tiles_fn(bool bf16, bool serve) {
   return bf16 ? (const void*)k_tiles<__nv_bfloat16, false> : (const void*)k_tiles<float, false>;
 }
 }  // namespace
-
-// Tensor maps of a tile buffer for the TMA row gathers: r_U ([n_u][kTile]),
-// t_V ([n_v][kTile]) and t_A ([n_a][kTile]); box kTile x 1.  Only the TMA
-// phases read them, so a build without them encodes nothing.
-int encode_tile_maps(TileBuf& t, uint32_t n_u, uint32_t n_v, uint32_t n_a) {
-  if (!AHPP_TMA) return 0;
-  typedef CUresult (*EncodeFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
-                               const cuuint64_t*, const cuuint32_t*, const cuuint32_t*,
-                               CUtensorMapInterleave, CUtensorMapSwizzle, CUtensorMapL2promotion,
-                               CUtensorMapFloatOOBfill);
-  static EncodeFn enc = nullptr;
-  if (!enc) {
-    void* fp = nullptr;
-    cudaDriverEntryPointQueryResult q;
-    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fp, 12000, cudaEnableDefault, &q) !=
-            cudaSuccess || q != cudaDriverEntryPointSuccess || !fp)
-      return -1;
-    enc = (EncodeFn)fp;
-  }
-  auto one = [&](CUtensorMap* m, float* base, uint32_t rows) {
-    const cuuint64_t dims[2] = {(cuuint64_t)kTile, (cuuint64_t)(rows ? rows : 1)};
-    const cuuint64_t strides[1] = {(cuuint64_t)kTile * 4};
-    const cuuint32_t box[2] = {(cuuint32_t)kTile, 1};
-    const cuuint32_t estr[2] = {1, 1};
-    return enc(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, base, dims, strides, box, estr,
-               CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
-               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
-  };
-  if (!one(&t.map_ru, t.r_u, n_u) || !one(&t.map_tv, t.t_v, n_v) || !one(&t.map_ta, t.t_a, n_a)) return -2;
-  return 0;
-}
 
 int launch_batch(const DevGraph& g, const BatchState& s, const BatchParams& p, bool bf16,
                  int grid, cudaStream_t stream) {

@@ -7,8 +7,6 @@
 // `groups` tiles run concurrently, each on its own slice of the persistent
 // grid with its own barrier; a group walks its tiles one after another.
 #pragma once
-#include <cuda.h>
-
 #include "../../include/ahpp.h"
 #include "ahpp_internal.cuh"
 
@@ -22,10 +20,8 @@ constexpr int kRadixBits = 8;      // top-k digit width (per-lane histograms of 
 constexpr int kRadixBins = 1 << kRadixBits;
 constexpr int kRadixPasses = 64 / kRadixBits;
 
-// Buffers of one concurrent group (one tile in flight), with the tensor maps
-// the TMA row gathers use ([rows][kTile] floats, box kTile x 1).
+// Buffers of one concurrent group (one tile in flight).
 struct alignas(64) TileBuf {
-  CUtensorMap map_ru, map_tv, map_ta;
   float *r_u = nullptr, *pi = nullptr, *pic = nullptr;   // [n_u][kTile]
   float *t_v = nullptr, *t_a = nullptr;                  // [n_v][kTile], [n_a][kTile]
   float* t_a2 = nullptr;                                 // second t_A buffer (pushed for the next round)
@@ -107,6 +103,5 @@ int launch_batch(const DevGraph& g, const BatchState& s, const BatchParams& p, b
 int launch_serve_step(const DevGraph& g, const BatchParams& p, const ServeParams& sv, bool bf16,
                       int grid, cudaStream_t stream);
 int batch_max_grid(bool bf16, int sm_count);
-int encode_tile_maps(TileBuf& t, uint32_t n_u, uint32_t n_v, uint32_t n_a);
 
 }  // namespace ahpp

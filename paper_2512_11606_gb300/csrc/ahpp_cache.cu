@@ -28,7 +28,7 @@ namespace ahpp {
 namespace {
 
 constexpr char kMagic[8] = {'A', 'H', 'P', 'P', 'G', 'R', 'F', '1'};
-constexpr uint32_t kVersion = 3;
+constexpr uint32_t kVersion = 4;
 
 struct CacheHeader {
   char magic[8];
@@ -50,8 +50,7 @@ void visit_graph_ptrs(ahpp_graph* g, F f) {
   f((const void**)&G.au_off); f((const void**)&G.au_idx); f((const void**)&G.au_w); f((const void**)&G.au_c);
   f((const void**)&G.ua_pc);
   f((const void**)&G.rnorm_u); f((const void**)&G.cnorm_a);
-  f((const void**)&G.vu_mid); f((const void**)&G.au_mid);
-  ItemList* lists[] = {&G.s1_v, &G.s1_a, &G.s1_u, &G.b_v, &G.b_a, &G.b_u, &G.m_v, &G.m_a, &G.m_u};
+  ItemList* lists[] = {&G.s1_v, &G.s1_a, &G.s1_u, &G.b_v, &G.b_a, &G.b_u};
   for (ItemList* L : lists) {
     f((const void**)&L->items);
     f((const void**)&L->split_nchunks);

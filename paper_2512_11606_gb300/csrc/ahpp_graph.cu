@@ -331,8 +331,6 @@ int build_graph(const ahpp_graph_desc* d, ahpp_graph* g) {
   HostItems i1v = build_items(dg_v, s1), i1a = build_items(dg_a, s1), i1u = build_items(dg_u, s1);
   HostItems ibv = build_units(dg_v, kUnitChunk), iba = build_units(dg_a, kUnitChunk),
             ibu = build_units(dg_u, kUnitChunk);
-  const ItemShape sm{256, 32, 256, 512};
-  HostItems imv = build_items(dg_v, sm), ima = build_items(dg_a, sm), imu = build_items(dg_u, sm);
 
   // 6. upload
   auto up = [&](const void* src, size_t bytes) -> void* {
@@ -368,19 +366,6 @@ int build_graph(const ahpp_graph_desc* d, ahpp_graph* g) {
     G.ua_w = up(a.data(), a.size() * 4);
     G.au_w = up(b.data(), b.size() * 4);
   }
-  {
-    const uint32_t u_half = nU / 2;
-    std::vector<uint32_t> vmid(std::max(nV, 1u)), amid(std::max(nA, 1u));
-    for (uint32_t v = 0; v < nV; ++v)
-      vmid[v] = (uint32_t)(std::lower_bound(vu_idx.begin() + vu_off[v], vu_idx.begin() + vu_off[v + 1], u_half) -
-                           vu_idx.begin());
-    for (uint32_t a = 0; a < nA; ++a)
-      amid[a] = (uint32_t)(std::lower_bound(au_idx.begin() + au_off[a], au_idx.begin() + au_off[a + 1], u_half) -
-                           au_idx.begin());
-    G.u_half = u_half;
-    G.vu_mid = (const uint32_t*)up(vmid.data(), vmid.size() * 4);
-    G.au_mid = (const uint32_t*)up(amid.data(), amid.size() * 4);
-  }
   G.au_c = (const float*)up(f_au_c.data(), f_au_c.size() * 4);
   G.ua_pc = (const float*)up(f_ua_pc.data(), f_ua_pc.size() * 4);
   G.rnorm_u = (const float*)up(rnorm.data(), rnorm.size() * 4);
@@ -394,7 +379,6 @@ int build_graph(const ahpp_graph_desc* d, ahpp_graph* g) {
   };
   up_items(i1v, G.s1_v); up_items(i1a, G.s1_a); up_items(i1u, G.s1_u);
   up_items(ibv, G.b_v); up_items(iba, G.b_a); up_items(ibu, G.b_u);
-  up_items(imv, G.m_v); up_items(ima, G.m_a); up_items(imu, G.m_u);
 
   g->h_u_old2new = u_o2n;
   g->h_u_new2old = u_n2o;

@@ -107,11 +107,24 @@ struct ahpp_graph {
   void* topk_scratch = nullptr;
   size_t topk_scratch_bytes = 0;
 
+  // failure-detection self-test: the next launch's grid barriers start with
+  // a counter that can never reach the block count (see reset_barrier)
+  std::atomic<int> wait_trap{0};
+
   void* alloc(size_t bytes);          // cudaMalloc + track (nullptr on failure)
   void release_all();
 };
 
 namespace ahpp {
+// Clear a grid barrier before a persistent launch on `stream`.  When the
+// graph's self-test trap is armed (ahpp_selftest_arm_wait_timeout) the
+// counter is set far above any grid size instead, so the launch's first
+// barrier never fills and every block's bounded spin runs out; the trap is
+// consumed by the first launch that sees it.
+int reset_barrier(ahpp_graph* g, GridBarrier* bar, cudaStream_t stream, bool keep_trap = false);
+// Zero if the barrier's error word is clear; kStatusWait if a wait gave up.
+// Synchronous (reads one word from the device on `stream`).
+int barrier_status(GridBarrier* bar, cudaStream_t stream, int* status);
 int build_graph(const ahpp_graph_desc* desc, ahpp_graph* g);
 int alloc_query_state(ahpp_graph* g);
 int run_lambda(ahpp_graph* g);

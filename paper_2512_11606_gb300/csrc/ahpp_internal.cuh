@@ -59,19 +59,12 @@ struct DevGraph {
   const float* ua_pc = nullptr;         // U->A push coefficient (1-alpha) beta w(u,a) / (sum_a' w(u,a') sum_u' w(u',a))
   const float* rnorm_u = nullptr;
   const float* cnorm_a = nullptr;
-  // first entry of each V->U / A->U row whose U id is >= u_half (rows are
-  // sorted by U id): the batched phase 1 gathers the two halves of U in two
-  // passes so that each pass's gather set fits in L2
-  const uint32_t* vu_mid = nullptr;
-  const uint32_t* au_mid = nullptr;
-  uint32_t u_half = 0;
   float alpha = 0.f;
   float k_attr = 0.f;                   // (1 - alpha) * beta
   // single-query (one row per lane / warp-cooperative) work items
   ItemList s1_v, s1_a, s1_u;
-  // batched row-group units, and the TMA items (up to 32 rows per item)
+  // batched row-group units
   ItemList b_v, b_a, b_u;
-  ItemList m_v, m_a, m_u;
 };
 
 template <typename WA>

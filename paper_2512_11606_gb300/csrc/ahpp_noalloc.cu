@@ -112,7 +112,7 @@ extern "C" int ahpp_query_dense_noalloc(ahpp_graph* g, uint32_t q, double eps, f
   cudaStream_t st = stream ? (cudaStream_t)stream : g->stream;
   Q1Params p = noalloc_params(g, g->h_u_old2new[q], eps);
   p.trace_cap = 0;
-  AHPP_CUDA(cudaMemsetAsync(s.bar, 0, sizeof(GridBarrier), st));
+  if (int rc = reset_barrier(g, s.bar, st)) return rc;
   const int e = launch_query1(g->dg, s, p, g->bf16, g->q1_grid, st);
   if (e) return cuda_fail((cudaError_t)e, "ahpp_query_dense_noalloc: launch");
   k_scatter_out<<<std::max(1, g->sm_count * 4), 256, 0, st>>>(s.pi, g->d_u_new2old, (uint32_t)g->n_u,
@@ -120,8 +120,12 @@ extern "C" int ahpp_query_dense_noalloc(ahpp_graph* g, uint32_t q, double eps, f
   AHPP_CUDA(cudaGetLastError());
   QCtl ctl;
   AHPP_CUDA(cudaMemcpyAsync(&ctl, s.ctl, sizeof(ctl), cudaMemcpyDeviceToHost, st));
-  AHPP_CUDA(cudaStreamSynchronize(st));
+  int bst = kStatusOk;
+  if (int rc = barrier_status(s.bar, st, &bst)) return rc;     // also waits for the stream
+  if (ctl.status == kStatusWait || bst == kStatusWait) {
+    set_error("ahpp_query_dense_noalloc: a device wait gave up");
+    return AHPP_ETIMEOUT;
+  }
   if (ctl.status == kStatusCap) return AHPP_ENOTCONVERGED;
-  if (ctl.status == kStatusWait) { set_error("a device wait gave up"); return AHPP_ETIMEOUT; }
   return AHPP_OK;
 }

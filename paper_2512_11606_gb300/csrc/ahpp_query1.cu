@@ -356,8 +356,11 @@ k_query1(const __grid_constant__ DevGraph g, const __grid_constant__ Q1State s,
     s.final_maxr_bits[0] = 0u;
     s.final_maxr_bits[1] = 0u;
   }
-  if (!grid_sync(s.bar, nb)) return;
-  if (leader && p.lambda_mode) {
+  // a barrier that gives up here skips the rounds; the leader still reports
+  // the status below, so the host never reads a previous call's control block
+  bool init_ok = grid_sync(s.bar, nb);
+  if (!init_ok) {
+  } else if (leader && p.lambda_mode) {
     RAcc* a0 = &s.racc[2];
     a0->marked = g.n_u;
     a0->marked_deg = p.e_tot;
@@ -375,16 +378,16 @@ k_query1(const __grid_constant__ DevGraph g, const __grid_constant__ Q1State s,
       s.r_u[p.q] = 1.f;
     }
   }
-  if (!grid_sync(s.bar, nb)) return;
+  if (init_ok) init_ok = grid_sync(s.bar, nb);
 
   int phase = (p.lambda_mode || p.pi_mode) ? kPhaseSync : kPhaseAsync;
-  int status = kStatusOk;
+  int status = init_ok ? kStatusOk : kStatusWait;
   int dense = p.lambda_mode ? 1 : 0;
   uint32_t rounds = 0, switch_round = 0, dense_rounds = 0;
   unsigned long long n_p = 0, pushes = 0;
   Partials part;
 
-  for (;;) {
+  for (; status == kStatusOk;) {
     RAcc* A = &s.racc[rounds % 3];
     const RAcc* P = &s.racc[(rounds + 2) % 3];
     const uint32_t marked = __ldcg(&P->marked);

@@ -68,3 +68,13 @@ extern "C" int ahpp_selftest_wait_timeout(int device, int* blocks_gave_up, int* 
   *context_ok = h[1] == 42u;
   return AHPP_OK;
 }
+
+// Arms the graph's wait trap: the next persistent launch on g (single query,
+// batch, no-allocation query, power iteration or a serving step) starts with
+// a grid barrier that can never fill, so its first wait, before any round,
+// runs out; the call that made the launch must report AHPP_ETIMEOUT.
+extern "C" int ahpp_selftest_arm_wait_timeout(ahpp_graph* g) {
+  if (!g) { set_error("ahpp_selftest_arm_wait_timeout: null graph"); return AHPP_EINVAL; }
+  g->wait_trap.store(1);
+  return AHPP_OK;
+}

@@ -207,7 +207,7 @@ int server_step(ahpp_server* s) {
   AHPP_CUDA(cudaMemcpyAsync(s->d_slots, s->h_slots, sizeof(SlotState) * s->n_slots,
                             cudaMemcpyHostToDevice, s->stream));
   AHPP_CUDA(cudaMemcpyAsync(s->d_live, live.data(), 4 * live.size(), cudaMemcpyHostToDevice, s->stream));
-  AHPP_CUDA(cudaMemsetAsync(s->d_bar, 0, sizeof(GridBarrier), s->stream));
+  if (int rc = reset_barrier(g, s->d_bar, s->stream)) return rc;
   BatchParams p;
   p.kmax = s->kmax;
   p.out_nodes = s->d_nodes;
@@ -235,7 +235,14 @@ int server_step(ahpp_server* s) {
   if (e) return cuda_fail((cudaError_t)e, "serving step launch");
   AHPP_CUDA(cudaMemcpyAsync(s->h_slots, s->d_slots, sizeof(SlotState) * s->n_slots,
                             cudaMemcpyDeviceToHost, s->stream));
-  AHPP_CUDA(cudaStreamSynchronize(s->stream));
+  int bst = kStatusOk;
+  if (int rc = barrier_status(s->d_bar, s->stream, &bst)) return rc;   // also waits for the step
+  if (bst == kStatusWait) {
+    // a device wait gave up: the step may have stopped part-way through its
+    // tiles, so no slot's state can be trusted; the loop fails every request
+    set_error("serving step: a device wait gave up (grid barrier timeout)");
+    return AHPP_ETIMEOUT;
+  }
   // 3. hand out finished results
   std::vector<uint32_t> fin;
   for (uint32_t slot = 0; slot < s->n_slots; ++slot)
@@ -317,8 +324,7 @@ int ahpp_server_start(ahpp_graph* g, const ahpp_server_opts* opts, ahpp_server**
   if (o.single_max) s->single_max = o.single_max;
   // slots: requested, else what the HBM budget leaves after the graph, else 8 tiles
   const DevGraph& G = g->dg;
-  const size_t n_split = std::max((size_t)G.b_v.n_split + G.b_a.n_split + G.b_u.n_split,
-                                  (size_t)G.m_v.n_split + G.m_a.n_split + G.m_u.n_split);
+  const size_t n_split = (size_t)G.b_v.n_split + G.b_a.n_split + G.b_u.n_split;
   const size_t tile_bytes = (size_t)G.n_u * kTile * 12 + (size_t)std::max(G.n_v, 1u) * kTile * 4 +
                             (size_t)std::max(G.n_a, 1u) * kTile * 4 + std::max<size_t>(n_split, 1) * (kTile + 1) * 4 +
                             (size_t)kRadixPasses * kTile * kRadixBins * 4 + (size_t)kTile * s->kmax * 8 + 4096;
@@ -376,7 +382,6 @@ int ahpp_server_start(ahpp_graph* g, const ahpp_server_opts* opts, ahpp_server**
       b.cand_cnt = (uint32_t*)s->dalloc(kTile * 4);
       ok = b.r_u && b.pi && b.pic && b.t_v && b.t_a && b.t_a2 && b.split_acc && b.split_cnt && b.racc &&
            b.hist && b.cand && b.cand_cnt;
-      if (ok) ok = encode_tile_maps(b, G.n_u, G.n_v, G.n_a) == 0;
       if (ok) {
         // the split accumulators and counters must start at zero (kept zero by the kernel)
         ok = cudaMemset(b.split_acc, 0, std::max<size_t>(n_split, 1) * kTile * 4) == cudaSuccess &&

@@ -75,6 +75,47 @@ LARGE = dict(n_u=5_000_000, n_v=5_000_000, n_e=200_000_000, gamma_u=2.0, gamma_v
              bf16=True, seed=3)
 
 
+def _choice_counts(rng: np.random.Generator, p: np.ndarray, size: int) -> np.ndarray:
+    """How often each index is drawn by size draws with probabilities p.
+
+    The same draws as Generator.choice(len(p), size, p=p) (one uniform per
+    draw, located in the normalised cumulative sum), counted per index; the
+    uniforms are located in sorted order, which leaves the counts unchanged
+    and keeps the lookups cache-friendly."""
+    cdf = p.cumsum()
+    cdf /= cdf[-1]
+    u = np.sort(rng.random(size))
+    return np.bincount(_searchsorted(cdf, u, right=True), minlength=p.shape[0])
+
+
+# The large graph's arrays hold 10^8 elements; torch's CPU sort and binary
+# search run on all host cores where numpy's run on one.  Both are exact: a
+# stable sort is unique, and a binary search has one answer.
+def _stable_argsort(a: np.ndarray) -> np.ndarray:
+    """The stable sorting permutation of a (equal values keep their order)."""
+    import torch
+    return torch.sort(torch.from_numpy(np.ascontiguousarray(a)), stable=True).indices.numpy()
+
+
+def _searchsorted(sorted_a: np.ndarray, v: np.ndarray, right: bool = False) -> np.ndarray:
+    """np.searchsorted(sorted_a, v, side="right" if right else "left")."""
+    import torch
+    return torch.searchsorted(torch.from_numpy(np.ascontiguousarray(sorted_a)),
+                              torch.from_numpy(np.ascontiguousarray(v)), right=right).numpy()
+
+
+def _sort(a: np.ndarray) -> np.ndarray:
+    """np.sort(a)."""
+    import torch
+    return torch.sort(torch.from_numpy(np.ascontiguousarray(a))).values.numpy()
+
+
+def _merge_runs(runs: list) -> np.ndarray:
+    """Merge sorted arrays with no value in common into one sorted array
+    (numpy's stable sort finds the sorted runs and merges them)."""
+    return runs[0] if len(runs) == 1 else np.sort(np.concatenate(runs), kind="stable")
+
+
 def power_law_degrees(rng: np.random.Generator, n: int, gamma: float,
                       total: int, cap: int) -> np.ndarray:
     """Degree sequence of n nodes, Zipf(gamma) shaped, capped, summing to total."""
@@ -93,12 +134,10 @@ def power_law_degrees(rng: np.random.Generator, n: int, gamma: float,
             raise RuntimeError("degree rescaling did not converge")
         p = d / d.sum()
         if diff > 0:
-            idx = rng.choice(n, size=diff, p=p)
-            np.add.at(d, idx, 1)
+            d += _choice_counts(rng, p, diff)
             d = np.minimum(d, cap)
         else:
-            idx = rng.choice(n, size=-diff, p=p)
-            np.subtract.at(d, idx, 1)
+            d -= _choice_counts(rng, p, -diff)
             d = np.maximum(d, 1)
         diff = int(total - d.sum())
     return d
@@ -125,12 +164,15 @@ def bipartite_edges(n_u: int, n_v: int, n_e: int, gamma_u: float, gamma_v: float
     su = np.repeat(np.arange(n_u, dtype=np.int64), du)
     sv = np.repeat(np.arange(n_v, dtype=np.int64), dv)
     rng_for(seed, _S_PAIR).shuffle(sv)
-    key = _unique(su * n_v + sv)
+    # the pair set is kept as sorted runs with no pair in common: the unique
+    # stub pairs, then the pairs each top-up round adds
+    runs = [_unique(su * n_v + sv)]
+    count = runs[0].shape[0]
     rng = rng_for(seed, _S_TOPUP)
     rounds = 0
-    while key.shape[0] < n_e:
+    while count < n_e:
         rounds += 1
-        need = n_e - key.shape[0]
+        need = n_e - count
         draw = max(need + need // 2, 1024)
         if rounds <= 16:
             eu = su[rng.integers(0, su.shape[0], size=draw)]
@@ -139,16 +181,22 @@ def bipartite_edges(n_u: int, n_v: int, n_e: int, gamma_u: float, gamma_v: float
             eu = rng.integers(0, n_u, size=draw)
             ev = rng.integers(0, n_v, size=draw)
         cand = eu * n_v + ev
-        # keep first occurrences (draw order) of pairs not yet present
-        pos = np.searchsorted(key, cand)
-        pos[pos == key.shape[0]] = 0
-        cand = cand[key[pos] != cand]
-        order = np.argsort(cand, kind="stable")
+        # keep the first occurrence (in draw order) of every pair not yet
+        # present: sort the draws once (stable, so equal pairs keep draw
+        # order), test membership with sorted needles, and mark the first of
+        # each run of equal pairs
+        order = _stable_argsort(cand)
         sc = cand[order]
-        first = np.ones(sc.shape[0], dtype=bool)
-        first[1:] = sc[1:] != sc[:-1]
-        cand = cand[np.sort(order[first])][:need]
-        key = np.sort(np.concatenate([key, cand]))
+        keep = np.ones(sc.shape[0], dtype=bool)
+        for run in runs:
+            pos = _searchsorted(run, sc)
+            pos[pos == run.shape[0]] = 0
+            keep &= run[pos] != sc
+        keep[1:] &= sc[1:] != sc[:-1]
+        cand = cand[_sort(order[keep])][:need]
+        runs.append(_sort(cand))
+        count += cand.shape[0]
+    key = _merge_runs(runs)
     return (key // n_v).astype(np.uint32), (key % n_v).astype(np.uint32)
 
 

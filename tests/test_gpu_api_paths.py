@@ -193,6 +193,80 @@ def test_device_wait_gives_up_and_context_survives(ahpp, tiny):
     assert r.rc == 0 and r.nodes.shape[0] == 5
 
 
+def test_wait_timeout_at_the_first_barrier_of_each_query_kernel(ahpp, tiny):
+    """The same bounded wait inside the query kernels: with the self-test trap
+    armed, the launch's first grid barrier (before any round) can never fill,
+    every block gives up after its bounded spin, and the call reports
+    AHPP_ETIMEOUT instead of a previous call's status; the next call works."""
+    torch = pytest.importorskip("torch")
+    G, og, lam = tiny["G"], tiny["og"], tiny["lam"]
+    q = 3
+    ref = og.push("asrp", ALPHA, BETA, q, 1e-6, lam=lam)
+    good, _, _ = G.query_dense(q, 1e-6)          # leaves status "converged" behind
+    # single query (plain path)
+    G.arm_wait_timeout()
+    with pytest.raises(ahpp.AhppError) as e:
+        G.query_dense(q, 1e-6)
+    assert e.value.code == ahpp.AHPP_ETIMEOUT
+    # single query into device buffers: the status arrives in the stats
+    dev = torch.device("cuda", 0)
+    nodes_t = torch.zeros(5, dtype=torch.int32, device=dev)
+    scores_t = torch.zeros(5, dtype=torch.float32, device=dev)
+    n_t = torch.zeros(1, dtype=torch.int32, device=dev)
+    st_t = torch.zeros((1, ahpp.STATS_BYTES), dtype=torch.uint8, device=dev)
+    G.arm_wait_timeout()
+    G.query_device(q, 1e-6, 5, nodes_t, scores_t, n_t, st_t, None)
+    torch.cuda.synchronize()
+    assert stats_of(ahpp, st_t)[0]["status"] == 2
+    # batched launch (two tiles, ragged): every query reports the wait
+    qs = [int(x) for x in synth.draw_queries(tiny["g"].n_u, 40, seed=97)]
+    G.arm_wait_timeout()
+    out = np.zeros((40, tiny["g"].n_u), np.float32)
+    st = (ahpp.Stats * 40)()
+    rc = ahpp.lib().ahpp_query_batch_dense(
+        G.handle, 40, np.ascontiguousarray(qs, np.uint32).ctypes.data_as(ctypes.POINTER(ctypes.c_uint32)),
+        np.full(40, 1e-6).ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+        out.ctypes.data_as(ctypes.POINTER(ctypes.c_float)), st)
+    assert rc == ahpp.AHPP_ETIMEOUT
+    assert all(st[i].status == 2 for i in range(40))
+    # Algorithm 1 mode
+    G.arm_wait_timeout()
+    with pytest.raises(ahpp.AhppError) as e:
+        G.power_iteration(q, 10)
+    assert e.value.code == ahpp.AHPP_ETIMEOUT
+    # the trap is one-shot and the graph keeps working
+    again, st2, rc = G.query_dense(q, 1e-6)
+    assert rc == 0 and st2["status"] == 0
+    assert np.abs(again.astype(np.float64) - ref.pi).max() <= TOL
+    assert np.abs(again - good).max() <= TOL
+    dense, stats, rc = G.query_batch_dense(qs, 1e-6)
+    assert rc == 0 and all(s["status"] == 0 for s in stats)
+
+
+def test_wait_timeout_fails_the_server(ahpp, tiny):
+    """A serving step whose wait gives up fails its requests with
+    AHPP_ETIMEOUT and stops the server; a new server on the graph works."""
+    G = tiny["G"]
+    qs = [int(x) for x in synth.draw_queries(tiny["g"].n_u, 40, seed=98)]
+    srv = ahpp.Server(G, max_slots=32, rounds_per_step=4, single_max=-1)
+    try:
+        G.arm_wait_timeout()
+        t = srv.submit(qs[0], 1e-6, 5)
+        # no timeout on the wait itself (-1): AHPP_ETIMEOUT here is the device's
+        rc = ahpp.lib().ahpp_wait(srv._h, t, -1, None, None, None, None)
+        assert rc == ahpp.AHPP_ETIMEOUT
+        assert "serving loop failed" in ahpp.lib().ahpp_last_error().decode()
+    finally:
+        srv.stop()
+    srv = ahpp.Server(G, max_slots=32, rounds_per_step=4, single_max=-1)
+    try:
+        t = srv.submit(qs[0], 1e-6, 5)
+        r = srv.wait(t, 5)
+        assert r.rc == 0 and r.nodes.shape[0] == 5
+    finally:
+        srv.stop()
+
+
 def test_graph_cache_round_trip(ahpp, tiny, tmp_path):
     """A saved graph loads back without the build: same sizes and lambda,
     same results; mismatched alpha and truncated, damaged or extended files

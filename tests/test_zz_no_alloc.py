@@ -57,3 +57,34 @@ def test_noalloc_rejects_graph_beyond_scratch(ahpp):
         assert e.value.code == ahpp.AHPP_EINVAL and "static scratch" in str(e.value)
     finally:
         G.close()
+
+
+def test_noalloc_on_a_caller_stream_and_after_a_wait_timeout(ahpp):
+    """A call on a stream the caller created gives the allocating path's
+    result; a call whose first device wait gives up (self-test trap) reports
+    AHPP_ETIMEOUT rather than the status an earlier call left in the shared
+    scratch, and the next call is correct again."""
+    torch = pytest.importorskip("torch")
+    g = synth.make_graph(**synth.TINY)
+    G = ahpp.Graph.from_arrays(g, attr_bf16=0)
+    try:
+        q = int(synth.draw_queries(g.n_u, 1, seed=22)[0])
+        ref, _, rc = G.query_dense(q, 1e-6)
+        assert rc == ahpp.AHPP_OK
+        stream = torch.cuda.Stream()
+        out = torch.empty(g.n_u, dtype=torch.float32, device="cuda")
+        out.fill_(-1.0)
+        stream.wait_stream(torch.cuda.current_stream())
+        assert G.query_dense_noalloc(q, 1e-6, out, stream=stream) == ahpp.AHPP_OK
+        got = out.cpu().numpy()
+        assert np.abs(got.astype(np.float64) - ref).max() <= TOL
+        G.arm_wait_timeout()
+        with pytest.raises(ahpp.AhppError) as e:
+            G.query_dense_noalloc(q, 1e-6, out, stream=stream)
+        assert e.value.code == ahpp.AHPP_ETIMEOUT
+        out.fill_(-1.0)
+        stream.wait_stream(torch.cuda.current_stream())
+        assert G.query_dense_noalloc(q, 1e-6, out, stream=stream) == ahpp.AHPP_OK
+        assert np.abs(out.cpu().numpy().astype(np.float64) - ref).max() <= TOL
+    finally:
+        G.close()
