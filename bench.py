@@ -54,8 +54,12 @@ def parse(argv=None):
     ap.add_argument("--graph", default="medium", choices=["medium", "tiny", "large"])
     ap.add_argument("--scale", type=float, default=1.0,
                     help="large graph only: scale |U|, |V|, |E| and |A| by this factor (scalability sweep)")
-    ap.add_argument("--ablation", type=int, default=0,
+    ap.add_argument("--ablation", type=int, default=3,
                     help="single-query ablation of the ASRP switch rule and APP on N queries (0: off)")
+    ap.add_argument("--no-exact", action="store_true",
+                    help="skip the exact AHPP references (oracle Algorithm 1) of the parity leg")
+    ap.add_argument("--cost-queries", type=int, default=4,
+                    help="queries whose bfloat16 precision cost is measured (exact AHPP, two graphs)")
     ap.add_argument("--serve-seconds", type=float, default=12.0,
                     help="open-loop serving window (0 disables the serving measurement)")
     ap.add_argument("--serve-load", type=float, default=0.8,
@@ -67,11 +71,7 @@ def parse(argv=None):
 
 def graph_spec(name, scale=1.0):
     if name == "large":
-        spec = dict(synth.LARGE)
-        if scale != 1.0:
-            for key in ("n_u", "n_v", "n_e", "n_a"):
-                spec[key] = max(1, int(round(spec[key] * scale)))
-        return spec
+        return synth.scaled(synth.LARGE, scale)
     return dict(synth.MEDIUM_BF16) if name == "medium" else dict(synth.TINY, bf16=True)
 
 
@@ -150,6 +150,40 @@ def cpu_oracle_sample(g, eps, n_queries, seed=11):
         "p50_ms": statistics.median(lat) * 1e3,
         "p99_ms": float(np.percentile(lat, 99)) * 1e3,
     }
+
+
+# Exact AHPP references (Algorithm 1 until (1 - alpha)^T <= 1e-10, FP64 oracle),
+# run in a pool forked before any CUDA use and collected after the GPU legs.
+_OG32 = None
+EXACT_TAIL = 1e-10
+
+
+def exact_T(alpha=ALPHA, tail=EXACT_TAIL):
+    return int(math.ceil(math.log(tail) / math.log(1.0 - alpha)))
+
+
+def _exact_worker(args):
+    which, q, T = args
+    og = _OG if which == "graph" else _OG32
+    return og.power_iteration(ALPHA, BETA, int(q), T)
+
+
+def start_exact_refs(g, spec, cpu, n_cost, processes):
+    """Start the oracle's exact AHPP of the CPU-baseline sample queries (on
+    the benchmarked graph) and, for the first n_cost of them, on the same
+    graph with its attribute weights left in FP32 (not rounded to bfloat16):
+    the precision cost of storing them as bfloat16 (reading C-7).  Forks its
+    workers now (call before CUDA is initialised); returns (pool, async
+    result, job list)."""
+    import oracle
+    global _OG32
+    jobs = [("graph", int(q), exact_T()) for q in cpu["queries"]]
+    if spec.get("bf16") and n_cost > 0:
+        g32 = synth.make_graph(**dict(spec, bf16=False))
+        _OG32 = oracle.OracleGraph.from_arrays(g32)
+        jobs += [("fp32", int(q), exact_T()) for q in cpu["queries"][:n_cost]]
+    pool = mp.get_context("fork").Pool(max(1, min(processes, len(jobs))))
+    return pool, pool.map_async(_exact_worker, jobs, chunksize=1), jobs
 
 
 def host_cores():
@@ -267,6 +301,31 @@ def round_bytes(info, lanes, bf16=True):
     graph = 2 * (4 + 4) * nE + (4 + wa + 4) * nEA + 4 * (2 * (nU + 1) + nV + 1)
     state = lanes * 4 * (nU + nV + 2 * nA + nV + nA + 2 * nU + 4 * nU)
     return graph + state
+
+
+def q1_round_bytes(info, bf16=True):
+    """Algorithmic DRAM bytes of one pull round of the single-query kernel.
+
+    Graph (once per round): phase 1 streams V->U (index + coefficient,
+    8 B/edge) and A->U (index + weight, 4 + 2 B/entry in bfloat16), phase 2
+    U->V (index + weight, 8 B/edge) and U->A (index + weight); the row
+    offsets of the four directions and the attribute normalisers.  State:
+    the residues gathered in phase 1 (each read once), t_V and t_A written
+    and read once, the residues read and written, the reserve and its Kahan
+    compensation read and written.
+    """
+    wa = 2 if bf16 else 4
+    nU, nV, nA, nE, nEA = (info[k] for k in ("n_u", "n_v", "n_a", "n_e", "n_ea"))
+    graph = 2 * 8 * nE + 2 * (4 + wa) * nEA + 4 * (2 * (nU + 1) + (nV + 1) + (nA + 1)) + 4 * (nU + nA)
+    state = 4 * (nU + 2 * nV + 2 * nA + 2 * nU + 4 * nU)
+    return graph + state
+
+
+def decode_stats(ahpp, raw):
+    """ahpp_stats records from a [n, sizeof(ahpp_stats)] byte tensor."""
+    ctype_to_np = {"c_uint": "u4", "c_ulong": "u8", "c_double": "f8", "c_int": "i4"}
+    return np.frombuffer(raw.cpu().numpy().view(np.uint8).tobytes(), dtype=np.dtype(
+        [(f.rstrip("_"), ctype_to_np[t.__name__]) for f, t in ahpp.Stats._fields_]))
 
 
 def topk_bytes(info, queries):
@@ -395,9 +454,15 @@ def run_ours(args, rank, world, local_rank):
     g = synth.make_graph(**spec)
 
     cpu = None
+    exact_pool = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         n = args.cpu_queries or min(16, host_cores())
         cpu = cpu_oracle_sample(g, args.eps, n)
+        if not args.no_exact:
+            # runs on the host cores while the GPU legs run (a few cores stay
+            # free for the launching thread, the serving loop and the sampler)
+            exact_pool = start_exact_refs(g, spec, cpu, args.cost_queries,
+                                          max(1, host_cores() - 4))
 
     torch.cuda.set_device(local_rank)
     dev = torch.device("cuda", local_rank)
@@ -444,10 +509,7 @@ def run_ours(args, rank, world, local_rank):
     clocks = clk.stop()
     launch_ms = [a.elapsed_time(b) for a, b in ev]
     dev_s = sum(launch_ms) / 1e3
-    st = stats_t.cpu().numpy().view(np.uint8)
-    ctype_to_np = {"c_uint": "u4", "c_ulong": "u8", "c_double": "f8", "c_int": "i4"}
-    stats = np.frombuffer(st.tobytes(), dtype=np.dtype(
-        [(f.rstrip("_"), ctype_to_np[t.__name__]) for f, t in ahpp.Stats._fields_]))
+    stats = decode_stats(ahpp, stats_t)
     rounds = stats["rounds"].astype(np.int64)
     tile = int(info["batch_tile"])
     tile_rounds = int(sum(rounds[i:i + tile].max() for i in range(0, B, tile)))
@@ -478,21 +540,35 @@ def run_ours(args, rank, world, local_rank):
         pn = torch.empty(args.k, dtype=torch.int32, device=dev)
         ps = torch.empty(args.k, dtype=torch.float32, device=dev)
         pc = torch.empty(1, dtype=torch.int32, device=dev)
-        G.query_device(int(pq[0]), args.eps, args.k, pn, ps, pc, None, stream)
+        pst = torch.empty((1, ahpp.STATS_BYTES), dtype=torch.uint8, device=dev)
+        G.query_device(int(pq[0]), args.eps, args.k, pn, ps, pc, pst, stream)
         stream.synchronize()
-        lat = []
+        lat, p_rounds, p_dense = [], [], []
         for q in pq[1:]:
             a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             with torch.cuda.stream(stream):
                 a.record(stream)
-            G.query_device(int(q), args.eps, args.k, pn, ps, pc, None, stream)
+            G.query_device(int(q), args.eps, args.k, pn, ps, pc, pst, stream)
             with torch.cuda.stream(stream):
                 b.record(stream)
             stream.synchronize()
             lat.append(a.elapsed_time(b))
+            sd = decode_stats(ahpp, pst)[0]
+            p_rounds.append(int(sd["rounds"]))
+            p_dense.append(int(sd["dense_rounds"]))
         plain = {"qps": 1e3 / statistics.mean(lat), "p50_ms": statistics.median(lat),
                  "p99_ms": float(np.percentile(lat, 99)), "queries": len(lat),
-                 "rounds_example": int(G.query(int(pq[1]), args.eps, 1).stats["rounds"])}
+                 "rounds_mean": statistics.mean(p_rounds), "dense_rounds_mean": statistics.mean(p_dense)}
+        # roofline of the plain path's kernel: algorithmic bytes of its pull
+        # rounds (push rounds are counted as zero: an underestimate) over the
+        # measured time of the whole call (k_query1 + top-k)
+        peak_p, peak_kind_p = measured_peak()
+        alg_p = statistics.mean(p_dense) * q1_round_bytes(info)
+        ach_p = alg_p / (statistics.mean(lat) / 1e3) / 1e9
+        plain["roofline"] = {"bound": "hbm", "kernel": "k_query1", "achieved": ach_p, "peak": peak_p,
+                             "unit": "GB/s", "frac": ach_p / peak_p,
+                             "algorithmic_bytes_per_pull_round": q1_round_bytes(info),
+                             "peak_source": f"{peak_kind_p} hbm_gbs (MEASURED_PEAKS.json)"}
 
     # serving: open-loop Poisson arrivals on the same graph (continuous batching)
     served = None
@@ -501,7 +577,17 @@ def run_ours(args, rank, world, local_rank):
 
     parity = None
     if cpu is not None:
-        parity = parity_vs_oracle(G, cpu, args.eps, args.k)
+        exact = exact32 = None
+        if exact_pool is not None:
+            pool, ar, jobs = exact_pool
+            try:
+                vals = ar.get(timeout=1800)
+                exact = [v for (w, _, _), v in zip(jobs, vals) if w == "graph"]
+                exact32 = [v for (w, _, _), v in zip(jobs, vals) if w == "fp32"]
+            finally:
+                pool.close()
+                pool.join()
+        parity = parity_vs_oracle(G, cpu, args.eps, args.k, exact, exact32)
 
     ablation = None
     if rank == 0 and args.ablation > 0:
@@ -553,50 +639,121 @@ def run_ours(args, rank, world, local_rank):
         "data": "synthetic (seeded Philox power-law graph; the paper's datasets are not available)",
         "config": workload_config(args, {"lambda": info["lambda"], "batch_groups": info["batch_groups"],
                                          "tile": info["batch_tile"]}),
+        "gpu_launches": K,
+        "clocks": clocks,
+        "cpu_baseline": cpu and {k: cpu[k] for k in ("value", "unit", "cores", "cpu_model", "kind", "sample")},
+        "e2e": e2e,
+        "roofline": roof,
+        "plain": plain,
+        "served": served,
+        "parity": parity,
+        "ablation": ablation,
         "p50_ms": statistics.median(lat_ms),
         "p99_ms": float(np.percentile(lat_ms, 99)),
         "latency_note": "batched: a query completes with its 1,024-query step",
-        "plain": plain,
-        "speedup_vs_plain": (value / world / plain["qps"]) if plain else None,
-        "served": served,
-        "served_speedup_vs_plain": (served["qps"] / plain["qps"]) if (plain and served) else None,
         "rounds_mean": float(rounds.mean()),
         "rounds_max": int(rounds.max()),
         "not_converged": int((stats["status"] != 0).sum()),
         "mass_err_max": float(stats["mass_err"].max()),
-        "roofline": roof,
-        "parity": parity,
-        "ablation": ablation,
-        "cpu_baseline": cpu and {k: cpu[k] for k in ("value", "unit", "cores", "cpu_model", "kind", "sample")},
-        "e2e": e2e,
-        "gpu_launches": K,
-        "clocks": clocks,
         "wall_s": wall,
     }
+    # the headline numbers, short and last on the line
+    sat = (served or {}).get("saturated") or {}
+    ol = (served or {}).get("open_loop") or {}
+    ex = (parity or {}).get("exact") or {}
+    pq = plain["qps"] if plain else None
+    out.update({
+        "batched_qps": _opt(value / world, 4),
+        "plain_qps": _opt(pq, 4),
+        "speedup_vs_plain": _opt(pq and value / world / pq, 3),
+        "served_qps": _opt(served and served["qps"], 4),
+        "served_p50_ms": _opt(sat.get("p50_ms"), 4),
+        "served_p99_ms": _opt(sat.get("p99_ms"), 4),
+        "served_speedup_vs_plain": _opt(pq and served and served["qps"] / pq, 3),
+        "served_open_loop_qps": _opt(ol.get("qps"), 4),
+        "served_open_loop_p50_ms": _opt(ol.get("p50_ms"), 4),
+        "served_open_loop_p99_ms": _opt(ol.get("p99_ms"), 4),
+        "hbm_frac_k_tiles": _opt(roof["frac"], 3),
+        "hbm_frac_k_query1": _opt(plain and plain["roofline"]["frac"], 3),
+        "parity_max_abs_err_vs_oracle": _opt(parity and parity["max_abs_err_vs_oracle"], 3),
+        "parity_max_err_vs_exact": _opt(ex.get("max_err_vs_exact"), 3),
+        "parity_min_err_vs_exact": _opt(ex.get("min_err_vs_exact"), 3),
+        "topk_overlap_vs_exact": ex.get("topk_overlap_vs_exact_min"),
+        "bf16_precision_cost_max": _opt(((parity or {}).get("bf16_precision_cost") or {}).get("max_abs"), 3),
+    })
     G.close()
     return out
 
 
-def parity_vs_oracle(G, cpu, eps, k):
-    """The oracle's sample queries through the batched GPU path: per query the
-    largest |gpu - oracle| over all of U and the top-k overlap (nodes whose
-    oracle score lies within 2 eps of the k-th count as ties)."""
+def topk_overlap(nodes, ref, k, eps):
+    """Overlap of a returned top-k with the top-k of the reference vector;
+    nodes whose reference score lies within 2 eps of the k-th score count as
+    interchangeable (ties of the approximation)."""
+    kk = min(k, ref.shape[0])
+    order = np.lexsort((np.arange(ref.shape[0]), -ref))
+    kth = ref[order[kk - 1]]
+    ok = set(np.nonzero(ref >= kth - 2 * eps)[0].tolist())
+    return len(set(np.asarray(nodes).tolist()) & ok) / kk
+
+
+def _r(x, d=3):
+    """x rounded to d significant digits (keeps the bench line short)."""
+    return float(f"{x:.{d}g}")
+
+
+def _opt(x, d=3):
+    """_r(x, d), or None when there is no value."""
+    return None if x is None or x is False else _r(float(x), d)
+
+
+def parity_vs_oracle(G, cpu, eps, k, exact=None, exact32=None):
+    """The oracle's sample queries through the batched GPU path.
+
+    vs the oracle push: per query the largest |gpu - oracle| over all of U
+    and the top-k overlap.  vs exact AHPP (the oracle's Algorithm 1 run until
+    (1 - alpha)^T <= 1e-10): Theorem 2 asks 0 <= pi - pi_hat <= eps, so the
+    largest and smallest pi - pi_hat per query, and the top-k overlap with
+    the exact top-k (the precision measure of Fig. 7).  bf16 precision cost:
+    for the queries in exact32, the largest |pi_exact(bf16 weights) -
+    pi_exact(FP32 weights)| and the top-k overlap between the two exact
+    vectors: how far storing the attribute weights as bfloat16 moves the
+    answer from the one the FP32 input defines."""
     qs = cpu["queries"]
     dense, _, _ = G.query_batch_dense(qs, eps)
     res = G.query_batch(qs, eps, k)
-    errs, overlaps = [], []
+    errs, overlaps, hi, lo, ov_ex = [], [], [], [], []
     for i, ref in enumerate(cpu["pi"]):
-        errs.append(float(np.abs(dense[i].astype(np.float64) - ref).max()))
-        kk = min(k, ref.shape[0])
-        order = np.lexsort((np.arange(ref.shape[0]), -ref))
-        kth = ref[order[kk - 1]]
-        ok = set(np.nonzero(ref >= kth - 2 * eps)[0].tolist())
-        got = set(res[i].nodes.tolist())
-        overlaps.append(len(got & ok) / kk)
-    return {"queries": len(qs), "eps": eps, "k": k, "bound_abs": 1e-6,
-            "max_abs_err_vs_oracle": max(errs), "per_query_max_abs_err": errs,
-            "topk_overlap_min": min(overlaps), "per_query_topk_overlap": overlaps,
-            "note": "batched GPU results of the CPU-baseline sample vs the FP64 oracle push"}
+        gpu = dense[i].astype(np.float64)
+        errs.append(float(np.abs(gpu - ref).max()))
+        overlaps.append(topk_overlap(res[i].nodes, ref, k, eps))
+        if exact is not None:
+            d = exact[i] - gpu
+            hi.append(float(d.max()))
+            lo.append(float(d.min()))
+            ov_ex.append(topk_overlap(res[i].nodes, exact[i], k, eps))
+    out = {"queries": len(qs), "eps": eps, "k": k, "bound_abs": 1e-6,
+           "max_abs_err_vs_oracle": max(errs), "per_query_max_abs_err": [_r(x) for x in errs],
+           "topk_overlap_min": min(overlaps),
+           "note": "batched GPU results of the CPU-baseline sample vs the FP64 oracle push"}
+    if exact is not None:
+        out["exact"] = {
+            "reference": f"oracle Algorithm 1, T = {exact_T()} ((1 - alpha)^T <= {EXACT_TAIL:g}), FP64",
+            "max_err_vs_exact": max(hi), "min_err_vs_exact": min(lo),
+            "per_query_max_err": [_r(x) for x in hi], "per_query_min_err": [_r(x) for x in lo],
+            "topk_overlap_vs_exact_min": min(ov_ex),
+            "bound": f"0 <= pi - pi_hat <= eps = {eps:g} (Theorem 2), FP32 rounding below"}
+    if exact32:
+        cost, ov = [], []
+        for i, e32 in enumerate(exact32):
+            cost.append(float(np.abs(exact[i] - e32).max()))
+            order = np.lexsort((np.arange(e32.shape[0]), -e32))
+            ov.append(topk_overlap(order[:k], exact[i], k, eps))
+        out["bf16_precision_cost"] = {
+            "queries": len(cost), "max_abs": max(cost), "per_query_max_abs": [_r(x) for x in cost],
+            "topk_overlap_min": min(ov),
+            "note": ("exact AHPP with the attribute weights rounded to bfloat16 (what the library "
+                     "stores) vs with the FP32 weights of the same graph, both by the FP64 oracle")}
+    return out
 
 
 def run_ablation(ahpp, g, args, lam, device):

@@ -116,6 +116,17 @@ def _merge_runs(runs: list) -> np.ndarray:
     return runs[0] if len(runs) == 1 else np.sort(np.concatenate(runs), kind="stable")
 
 
+def scaled(spec: dict, factor: float) -> dict:
+    """A workload shape with |U|, |V|, |E| and |A| scaled by factor (the
+    attributes per node, exponents, weight laws and seed unchanged): the
+    scalability sweep's graphs and the reduced large graph of the tests."""
+    out = dict(spec)
+    if factor != 1.0:
+        for key in ("n_u", "n_v", "n_e", "n_a"):
+            out[key] = max(1, int(round(out[key] * factor)))
+    return out
+
+
 def power_law_degrees(rng: np.random.Generator, n: int, gamma: float,
                       total: int, cap: int) -> np.ndarray:
     """Degree sequence of n nodes, Zipf(gamma) shaped, capped, summing to total."""
