@@ -56,6 +56,8 @@ def parse(argv=None):
                     help="large graph only: scale |U|, |V|, |E| and |A| by this factor (scalability sweep)")
     ap.add_argument("--ablation", type=int, default=3,
                     help="single-query ablation of the ASRP switch rule and APP on N queries (0: off)")
+    ap.add_argument("--no-autotune", action="store_true",
+                    help="keep the default launch shapes (no ahpp_autotune before the timed region)")
     ap.add_argument("--no-exact", action="store_true",
                     help="skip the exact AHPP references (oracle Algorithm 1) of the parity leg")
     ap.add_argument("--cost-queries", type=int, default=4,
@@ -307,17 +309,21 @@ def q1_round_bytes(info, bf16=True):
     """Algorithmic DRAM bytes of one pull round of the single-query kernel.
 
     Graph (once per round): phase 1 streams V->U (index + coefficient,
-    8 B/edge) and A->U (index + weight, 4 + 2 B/entry in bfloat16), phase 2
-    U->V (index + weight, 8 B/edge) and U->A (index + weight); the row
-    offsets of the four directions and the attribute normalisers.  State:
-    the residues gathered in phase 1 (each read once), t_V and t_A written
-    and read once, the residues read and written, the reserve and its Kahan
-    compensation read and written.
+    8 B/edge); phase 2 streams U->V (index + weight, 8 B/edge) and U->A
+    (index + weight, 4 + 2 B/entry in bfloat16); the row offsets; the
+    attribute normalisers.  With the attribute push (single_attr_push) the
+    attribute hop reuses phase 2's U->A stream; without it phase 1 also
+    streams A->U (index + FP32 pull coefficient, 8 B/entry).  State: the
+    residues gathered in phase 1 (each read once), t_V written and read,
+    t_A read, written (or pushed) and cleared, the residues read and written,
+    the reserve and its Kahan compensation read and written.
     """
     wa = 2 if bf16 else 4
     nU, nV, nA, nE, nEA = (info[k] for k in ("n_u", "n_v", "n_a", "n_e", "n_ea"))
-    graph = 2 * 8 * nE + 2 * (4 + wa) * nEA + 4 * (2 * (nU + 1) + (nV + 1) + (nA + 1)) + 4 * (nU + nA)
-    state = 4 * (nU + 2 * nV + 2 * nA + 2 * nU + 4 * nU)
+    graph = 2 * 8 * nE + (4 + wa) * nEA + 4 * (2 * (nU + 1) + (nV + 1)) + 4 * (nU + nA)
+    if not info.get("single_attr_push", 0):
+        graph += 8 * nEA + 4 * (nA + 1)
+    state = 4 * (nU + 2 * nV + 3 * nA + 2 * nU + 4 * nU)
     return graph + state
 
 
@@ -467,6 +473,12 @@ def run_ours(args, rank, world, local_rank):
     torch.cuda.set_device(local_rank)
     dev = torch.device("cuda", local_rank)
     G = ahpp.Graph.from_arrays(g, device=local_rank)
+    tune = None
+    if not args.no_autotune:
+        # launch shapes tuned on a sample of the workload's queries (device-timed)
+        t0 = time.perf_counter()
+        G.autotune(synth.draw_queries(g.n_u, 32, seed=13 + rank), args.eps)
+        tune = time.perf_counter() - t0
     info = G.info
     stream = torch.cuda.Stream(device=dev)
     B, K, W = args.batch, args.steps, args.warmup
@@ -637,8 +649,14 @@ def run_ours(args, rank, world, local_rank):
         "vs_baseline": None,
         "dtype": "f32",
         "data": "synthetic (seeded Philox power-law graph; the paper's datasets are not available)",
-        "config": workload_config(args, {"lambda": info["lambda"], "batch_groups": info["batch_groups"],
-                                         "tile": info["batch_tile"]}),
+        "config": workload_config(args, {
+            "lambda": info["lambda"], "tile": info["batch_tile"], "batch_groups": info["batch_groups"],
+            "batch_chunk": info["batch_chunk"],
+            "single_dense_div": info["single_dense_div"], "single_attr_push": info["single_attr_push"],
+            "single_vec_width": info["single_vec_width"],
+            "autotune_s": tune and round(tune, 1),
+            "autotune_ms_per_query": tune and {k: _r(v, 3) for k, v in G.autotune_report().items()},
+            "launch_shape": "ahpp_autotune on 32 sample queries" if tune else "defaults"}),
         "gpu_launches": K,
         "clocks": clocks,
         "cpu_baseline": cpu and {k: cpu[k] for k in ("value", "unit", "cores", "cpu_model", "kind", "sample")},

@@ -82,8 +82,13 @@ typedef struct {
     uint64_t hbm_budget_bytes; /* cap on device memory of graph + query state; 0 = no cap */
     int device;                /* CUDA device ordinal (default 0) */
     uint32_t max_rounds;       /* round cap per query; 0: automatic */
-    uint32_t batch_tile;       /* queries per batched tile: 0 or 32 (the width the library is built for) */
+    uint32_t batch_tile;       /* queries per batched tile: 16 or 32; 0: 32 (ahpp_autotune picks one);
+                                  serving always uses tiles of 32 */
     uint32_t batch_groups;     /* tiles processed concurrently, 1..8; 0: 1 (ahpp_autotune picks 1, 2 or 4) */
+    uint32_t batch_chunk;      /* entries per chunk of a long row in the batched kernel: 128, 256 or
+                                  512; 0: 256 (ahpp_autotune picks one) */
+    uint32_t single_vec_width; /* single-query kernel: at most this many lanes walk one short row
+                                  (1, 2, 4, 8, 16 or 32); 0: 32 (ahpp_autotune picks one) */
 } ahpp_config;
 
 /* Per-query statistics. */
@@ -113,6 +118,14 @@ typedef struct {
     int device;
     int sm_count;
     uint32_t batch_tile, batch_groups;   /* batched launch shape in use */
+    uint32_t batch_chunk;                /* batched: entries per chunk of a long row */
+    /* single-query kernel (the plain path): pull rounds once the frontier's
+     * degree sum exceeds 1/single_dense_div of |E| + |E_A|; the attribute hop
+     * of pull rounds pushed from phase 2 through shared memory (1) or pulled
+     * over A->U (0); rows of up to 64 entries walked by at most
+     * single_vec_width lanes each (1 = one row per lane); single_smem_bytes
+     * of shared memory per block. */
+    uint32_t single_dense_div, single_attr_push, single_vec_width, single_smem_bytes;
 } ahpp_graph_info;
 
 /* Serving options. */
@@ -241,11 +254,30 @@ int ahpp_query_device(ahpp_graph *g, uint32_t q, double eps, uint32_t k,
                       uint32_t *d_out_nodes, float *d_out_scores, uint32_t *d_out_n,
                       ahpp_stats *d_stats, void *stream);
 
-/* Autotune the batched launch shape (tiles processed concurrently: 1, 2 or
- * 4) by timing the sample, replicated to fill every candidate; the choice is
- * stored in the graph and reported by ahpp_get_graph_info.  q_sample: host
- * array of n_sample query ids (n_sample == 0 changes nothing). */
+/* Autotune the launch shapes on a sample of the caller's queries, timing
+ * every candidate on the device (CUDA events on the graph's stream), one
+ * knob at a time with the others fixed.  Batched kernel, on the sample
+ * replicated to fill four tiles of 32: queries per tile (32, 16), entries per
+ * chunk of a long row (128, 256, 512), then tiles processed concurrently
+ * (1, 2, 4).  Single-query kernel, on
+ * up to four sample queries: lanes per short row (32, 8, 2, 1: at most that
+ * many lanes walk one row), then the frontier fraction 1/dense_div (8, 16,
+ * 32, 64, 128) past which rounds run as pull sweeps.  Every candidate gives the same results
+ * within FP32 rounding (only the order of sums changes).  The choice is
+ * stored in the graph and reported by ahpp_get_graph_info; the measured
+ * times by ahpp_autotune_report.  Do not run it while a server on g is
+ * running.  q_sample: host array of n_sample query ids (n_sample == 0
+ * changes nothing).  AHPP_EINVAL for a NULL g or q_sample, an id outside U
+ * or a bad eps. */
 int ahpp_autotune(ahpp_graph *g, uint32_t n_sample, const uint32_t *q_sample, double eps);
+
+/* The last ahpp_autotune's measurements as a JSON object text, one entry
+ * "knob=value": milliseconds of device time per query (the batched launch's
+ * time over its queries; a single query's time), in the order measured.
+ * Copies at most cap - 1 bytes and a terminating zero into buf (host) when
+ * buf and cap are given; *len (nullable) receives the full length.  "" if
+ * the graph was never tuned.  AHPP_EINVAL for a NULL g. */
+int ahpp_autotune_report(const ahpp_graph *g, char *buf, size_t cap, size_t *len);
 
 /* Serving (continuous batching).  A server owns a pool of device slots
  * (one query each, in tiles of 32) sized by opts->max_slots or the HBM

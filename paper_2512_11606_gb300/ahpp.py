@@ -44,7 +44,8 @@ class Config(ctypes.Structure):
                 ("attr_bf16", ctypes.c_int), ("kahan", ctypes.c_int),
                 ("switch_rule", ctypes.c_int), ("hbm_budget_bytes", ctypes.c_uint64),
                 ("device", ctypes.c_int), ("max_rounds", ctypes.c_uint32),
-                ("batch_tile", ctypes.c_uint32), ("batch_groups", ctypes.c_uint32)]
+                ("batch_tile", ctypes.c_uint32), ("batch_groups", ctypes.c_uint32),
+                ("batch_chunk", ctypes.c_uint32), ("single_vec_width", ctypes.c_uint32)]
 
 
 class Stats(ctypes.Structure):
@@ -66,7 +67,10 @@ class GraphInfo(ctypes.Structure):
                 ("lambda_T", ctypes.c_uint32), ("graph_bytes", ctypes.c_uint64),
                 ("query_state_bytes", ctypes.c_uint64), ("tile_state_bytes", ctypes.c_uint64),
                 ("device", ctypes.c_int), ("sm_count", ctypes.c_int),
-                ("batch_tile", ctypes.c_uint32), ("batch_groups", ctypes.c_uint32)]
+                ("batch_tile", ctypes.c_uint32), ("batch_groups", ctypes.c_uint32),
+                ("batch_chunk", ctypes.c_uint32),
+                ("single_dense_div", ctypes.c_uint32), ("single_attr_push", ctypes.c_uint32),
+                ("single_vec_width", ctypes.c_uint32), ("single_smem_bytes", ctypes.c_uint32)]
 
 
 class ServerOpts(ctypes.Structure):
@@ -106,6 +110,8 @@ SIGNATURES = {
                                          _vp, _vp, _vp, _vp, _vp]),
     "ahpp_query_dense_noalloc": (ctypes.c_int, [_vp, ctypes.c_uint32, ctypes.c_double, _vp, _vp]),
     "ahpp_autotune": (ctypes.c_int, [_vp, ctypes.c_uint32, _u32p, ctypes.c_double]),
+    "ahpp_autotune_report": (ctypes.c_int, [_vp, ctypes.c_char_p, ctypes.c_size_t,
+                                            ctypes.POINTER(ctypes.c_size_t)]),
     "ahpp_server_start": (ctypes.c_int, [_vp, ctypes.POINTER(ServerOpts), ctypes.POINTER(_vp)]),
     "ahpp_submit": (ctypes.c_int, [_vp, ctypes.c_uint32, ctypes.c_double, ctypes.c_uint32,
                                    _u64p]),
@@ -333,6 +339,15 @@ class Graph:
         _check(lib().ahpp_autotune(self._h, q.shape[0], _p(q, _u32p), eps))
         self.info = self.get_info()
         return self.info
+
+    def autotune_report(self) -> dict:
+        """ms of device time per query of every candidate the last autotune timed."""
+        n = ctypes.c_size_t(0)
+        _check(lib().ahpp_autotune_report(self._h, None, 0, ctypes.byref(n)))
+        buf = ctypes.create_string_buffer(n.value + 1)
+        _check(lib().ahpp_autotune_report(self._h, buf, n.value + 1, None))
+        import json
+        return json.loads(buf.value.decode() or "{}")
 
 
 STATS_BYTES = ctypes.sizeof(Stats)

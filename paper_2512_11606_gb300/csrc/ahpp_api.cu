@@ -93,9 +93,13 @@ Q1Params q1_params(const ahpp_graph* g, uint32_t q_new, double eps) {
   p.log_inv = std::log(1.0 / (1.0 - g->cfg.alpha));
   p.e_tot = (uint32_t)(g->n_e + g->n_ea);
   p.max_rounds = g->cfg.max_rounds ? g->cfg.max_rounds : auto_rounds(p.eps_f, g->cfg.alpha);
-  p.dense_div = 32;
+  p.dense_div = g->q1_dense_div;
   p.n_split = g->n_split1;
   p.trace_cap = 4096;
+  p.smem_bytes = g->q1_smem;
+  p.attr_push = g->q1_attr_push;
+  p.ta_smem = g->q1_ta_smem;
+  p.vw_max = g->q1_vw_max;
   return p;
 }
 
@@ -179,12 +183,21 @@ int run_lambda(ahpp_graph* g) {
   return AHPP_OK;
 }
 
+int batch_plan(ahpp_graph* g, BatchParams& p) {
+  if (g->bt_grid <= 0) {
+    g->bt_grid = batch_max_grid(g->bf16, g->sm_count);
+    if (g->bt_grid <= 0) { set_error("batched occupancy query failed"); return AHPP_ECUDA; }
+  }
+  (void)p;
+  return AHPP_OK;
+}
+
 int ensure_batch(ahpp_graph* g, uint32_t groups, uint32_t kmax) {
   BatchState& s = g->bt;
   kmax = std::max<uint32_t>(kmax, 1);
   if (s.n_groups >= groups && s.kmax_cap >= kmax) return AHPP_OK;
   const DevGraph& G = g->dg;
-  const size_t n_split = (size_t)G.b_v.n_split + G.b_a.n_split + G.b_u.n_split;
+  const size_t n_split = G.b_split_max;        // any chunk choice fits
   const uint32_t kcap = std::max(kmax, s.kmax_cap);
   const uint32_t ng = std::max(groups, s.n_groups);
   uint64_t bytes = 0;
@@ -229,13 +242,10 @@ int run_batch_launch(ahpp_graph* g, uint32_t n, const uint32_t* d_q, const doubl
   const uint32_t groups = std::max<uint32_t>(1, std::min<uint32_t>(g->batch_groups, kMaxGroups));
   int rc = ensure_batch(g, groups, kmax);
   if (rc) return rc;
-  if (g->bt_grid <= 0) {
-    g->bt_grid = batch_max_grid(g->bf16, g->sm_count);
-    if (g->bt_grid <= 0) { set_error("batched occupancy query failed"); return AHPP_ECUDA; }
-  }
+  BatchParams p;
+  if ((rc = batch_plan(g, p))) return rc;
   const int grid = g->bt_grid / (int)groups * (int)groups;
   if (grid < (int)groups) { set_error("grid too small for the group count"); return AHPP_EINVAL; }
-  BatchParams p;
   p.n = n;
   p.q = d_q;
   p.eps = d_eps;
@@ -258,6 +268,7 @@ int run_batch_launch(ahpp_graph* g, uint32_t n, const uint32_t* d_q, const doubl
   p.max_rounds = g->cfg.max_rounds ? g->cfg.max_rounds
                                    : auto_rounds(1e-14 / std::max(g->lambda, 1.0), g->cfg.alpha);
   p.groups = groups;
+  p.tile = g->batch_tile;
   for (uint32_t i = 0; i < groups; ++i)
     if (int rc = reset_barrier(g, g->bt.tb[i].bar, stream, i + 1 < groups)) return rc;
   int e = launch_batch(g->dg, g->bt, p, g->bf16, grid, stream);
@@ -375,12 +386,20 @@ int ahpp_load_graph(const ahpp_graph_desc* desc, const ahpp_config* cfg, ahpp_gr
     set_error("ahpp_load_graph: alpha must be in (0,1), beta in [0,1], algo APP or ASRP");
     return AHPP_EINVAL;
   }
-  if (c.batch_tile != 0 && c.batch_tile != 32) {
-    set_error("ahpp_load_graph: batch_tile must be 0 or 32");
+  if (c.batch_tile != 0 && c.batch_tile != 16 && c.batch_tile != 32) {
+    set_error("ahpp_load_graph: batch_tile must be 0, 16 or 32");
     return AHPP_EINVAL;
   }
   if (c.batch_groups > (uint32_t)kMaxGroups) {
     set_error("ahpp_load_graph: batch_groups must be at most 8");
+    return AHPP_EINVAL;
+  }
+  if (chunk_choice(c.batch_chunk) < 0) {
+    set_error("ahpp_load_graph: batch_chunk must be 0, 128, 256 or 512");
+    return AHPP_EINVAL;
+  }
+  if (c.single_vec_width > 32 || (c.single_vec_width & (c.single_vec_width - 1))) {
+    set_error("ahpp_load_graph: single_vec_width must be 0 or a power of two up to 32");
     return AHPP_EINVAL;
   }
   int ndev = 0;
@@ -394,14 +413,16 @@ int ahpp_load_graph(const ahpp_graph_desc* desc, const ahpp_config* cfg, ahpp_gr
   ahpp_graph* g = new ahpp_graph();
   g->cfg = c;
   g->device = c.device;
-  g->batch_tile = ahpp::kTile;
+  g->batch_tile = c.batch_tile ? c.batch_tile : (uint32_t)ahpp::kTile;
   g->batch_groups = c.batch_groups ? c.batch_groups : 1;
+  g->q1_vw_max = c.single_vec_width ? c.single_vec_width : 32;
   int rc = AHPP_OK;
   if (cudaDeviceGetAttribute(&g->sm_count, cudaDevAttrMultiProcessorCount, c.device) != cudaSuccess ||
       cudaStreamCreateWithFlags(&g->stream, cudaStreamNonBlocking) != cudaSuccess) {
     rc = cuda_fail(cudaGetLastError(), "ahpp_load_graph: device setup");
   }
   if (rc == AHPP_OK) rc = build_graph(desc, g);
+  if (rc == AHPP_OK) select_chunk(g->dg, (uint32_t)chunk_choice(c.batch_chunk));
   if (rc == AHPP_OK) {
     if (c.algo == AHPP_ASRP && !(c.lambda > 0.0)) rc = run_lambda(g);
     else g->lambda = c.lambda > 0.0 ? c.lambda : 1.0;
@@ -439,6 +460,11 @@ int ahpp_get_graph_info(const ahpp_graph* g, ahpp_graph_info* info) {
   info->sm_count = g->sm_count;
   info->batch_tile = g->batch_tile;
   info->batch_groups = g->batch_groups;
+  info->batch_chunk = kChunkSizes[g->dg.b_chunk];
+  info->single_dense_div = g->q1_dense_div;
+  info->single_attr_push = (uint32_t)g->q1_attr_push;
+  info->single_vec_width = g->q1_vw_max;
+  info->single_smem_bytes = g->q1_smem;
   return AHPP_OK;
 }
 
@@ -667,35 +693,141 @@ int ahpp_query_batch_dense(ahpp_graph* g, uint32_t n, const uint32_t* q, const d
 
 }  // extern "C"
 
+namespace {
+
+// Device time (ms, CUDA events on the graph's stream) of one batched launch
+// of the n queries already in io->q / io->eps, with the graph's current
+// launch shape; no outputs besides the stats.
+int time_batch(ahpp_graph* g, GraphIo* io, uint32_t n, float* ms) {
+  cudaEvent_t a, b;
+  AHPP_CUDA(cudaEventCreate(&a));
+  AHPP_CUDA(cudaEventCreate(&b));
+  int rc = AHPP_OK;
+  if (cudaEventRecord(a, g->stream) != cudaSuccess) rc = cuda_fail(cudaGetLastError(), "autotune event");
+  if (rc == AHPP_OK)
+    rc = run_batch_launch(g, n, (const uint32_t*)io->q.p, (const double*)io->eps.p, nullptr, 0, nullptr,
+                          nullptr, nullptr, (ahpp_stats*)io->stats.p, nullptr, g->stream);
+  if (rc == AHPP_OK && (cudaEventRecord(b, g->stream) != cudaSuccess || cudaEventSynchronize(b) != cudaSuccess ||
+                        cudaEventElapsedTime(ms, a, b) != cudaSuccess))
+    rc = cuda_fail(cudaGetLastError(), "autotune timing");
+  cudaEventDestroy(a);
+  cudaEventDestroy(b);
+  return rc;
+}
+
+// Device time of single queries (k_query1 + nothing else) over the sample.
+int time_single(ahpp_graph* g, const std::vector<uint32_t>& qs, double eps, float* ms) {
+  cudaEvent_t a, b;
+  AHPP_CUDA(cudaEventCreate(&a));
+  AHPP_CUDA(cudaEventCreate(&b));
+  int rc = AHPP_OK;
+  if (cudaEventRecord(a, g->stream) != cudaSuccess) rc = cuda_fail(cudaGetLastError(), "autotune event");
+  for (size_t i = 0; rc == AHPP_OK && i < qs.size(); ++i)
+    rc = run_query1_launch(g, g->h_u_old2new[qs[i]], eps, g->stream);
+  if (rc == AHPP_OK && (cudaEventRecord(b, g->stream) != cudaSuccess || cudaEventSynchronize(b) != cudaSuccess ||
+                        cudaEventElapsedTime(ms, a, b) != cudaSuccess))
+    rc = cuda_fail(cudaGetLastError(), "autotune timing");
+  cudaEventDestroy(a);
+  cudaEventDestroy(b);
+  return rc;
+}
+
+}  // namespace
+
 extern "C" int ahpp_autotune(ahpp_graph* g, uint32_t n_sample, const uint32_t* q_sample, double eps) {
+  ahpp::NvtxRange nvtx_range_("ahpp_autotune");
   if (!g || (n_sample && !q_sample)) { ahpp::set_error("null argument"); return AHPP_EINVAL; }
   if (n_sample == 0) return AHPP_OK;
-  // candidate launch shapes: concurrent tiles (groups) in {1, 2, 4}; each is
-  // timed on the same sample of queries (replicated to fill every group)
-  const uint32_t cands[3] = {1, 2, 4};
-  double best = -1.0;
-  uint32_t best_g = g->batch_groups;
-  std::vector<double> eps_v;
-  std::vector<uint32_t> k_v, q_v;
-  for (uint32_t gi : cands) {
-    if (gi > (uint32_t)ahpp::kMaxGroups) continue;
-    const uint32_t n = std::max<uint32_t>(n_sample, gi * ahpp::kTile);
-    q_v.resize(n);
-    for (uint32_t i = 0; i < n; ++i) q_v[i] = q_sample[i % n_sample];
-    eps_v.assign(n, eps);
-    k_v.assign(n, 0);
-    const uint32_t saved = g->batch_groups;
-    g->batch_groups = gi;
-    std::vector<ahpp_stats> st(n);
-    auto t0 = std::chrono::steady_clock::now();
-    int rc = ahpp_query_batch(g, n, q_v.data(), eps_v.data(), nullptr, nullptr, nullptr, nullptr,
-                              st.data());
-    auto t1 = std::chrono::steady_clock::now();
-    g->batch_groups = saved;
-    if (rc != AHPP_OK && rc != AHPP_ENOTCONVERGED) return rc;
-    const double qps = n / std::chrono::duration<double>(t1 - t0).count();
-    if (qps > best) { best = qps; best_g = gi; }
+  if (int rc = check_eps(eps)) return rc;
+  for (uint32_t i = 0; i < n_sample; ++i)
+    if (q_sample[i] >= g->n_u) { ahpp::set_error("q_sample holds a node outside U"); return AHPP_EINVAL; }
+  std::lock_guard<std::mutex> lock(g->mu);
+  AHPP_CUDA(cudaSetDevice(g->device));
+  GraphIo* io = io_of(g);
+  int rc;
+  std::string log = "{";
+  auto note = [&](const char* knob, uint32_t v, float t) {
+    if (log.size() > 1) log += ", ";
+    log += "\"" + std::string(knob) + "=" + std::to_string(v) + "\": " + std::to_string(t);
+  };
+  // ---- batched launch shape, one knob at a time (hub rows in shared memory,
+  // entries per chunk of a long row, concurrent tile groups), every candidate
+  // on the same queries: the sample replicated to fill four tiles; one
+  // warm-up launch first
+  const uint32_t n = std::max<uint32_t>(n_sample, 4 * (uint32_t)kTile);
+  std::vector<uint32_t> qv(n);
+  for (uint32_t i = 0; i < n; ++i) qv[i] = q_sample[i % n_sample];
+  std::vector<double> ev(n, eps);
+  if ((rc = ensure(g, io->q, 4ull * n)) || (rc = ensure(g, io->eps, 8ull * n)) ||
+      (rc = ensure(g, io->stats, sizeof(ahpp_stats) * n)))
+    return rc;
+  AHPP_CUDA(cudaMemcpyAsync(io->q.p, qv.data(), 4ull * n, cudaMemcpyHostToDevice, g->stream));
+  AHPP_CUDA(cudaMemcpyAsync(io->eps.p, ev.data(), 8ull * n, cudaMemcpyHostToDevice, g->stream));
+  float ms = 0.f;
+  if ((rc = time_batch(g, io, n, &ms)) != AHPP_OK) return rc;
+  // try each value of one knob with the others fixed; keep the fastest
+  auto tune_batch = [&](const char* knob, auto set, const std::vector<uint32_t>& values) -> int {
+    float best = -1.f;
+    uint32_t best_v = values[0];
+    for (uint32_t v : values) {
+      set(v);
+      float t = 0.f;
+      if (int r = time_batch(g, io, n, &t)) return r;
+      note(knob, v, t / (float)n);
+      if (best < 0.f || t < best) { best = t; best_v = v; }
+    }
+    set(best_v);
+    return AHPP_OK;
+  };
+  const uint32_t saved_groups = g->batch_groups, saved_chunk = g->dg.b_chunk, saved_tile = g->batch_tile;
+  rc = tune_batch("batch_tile", [&](uint32_t v) { g->batch_tile = v; }, {(uint32_t)kTile, (uint32_t)kTileNarrow});
+  if (rc == AHPP_OK)
+    rc = tune_batch("batch_chunk_choice", [&](uint32_t v) { select_chunk(g->dg, v); }, {1u, 0u, 2u});
+  if (rc == AHPP_OK) rc = tune_batch("batch_groups", [&](uint32_t v) { g->batch_groups = v; }, {1u, 2u, 4u});
+  if (rc != AHPP_OK) {
+    g->batch_groups = saved_groups;
+    select_chunk(g->dg, saved_chunk);
+    g->batch_tile = saved_tile;
+    return rc;
   }
-  g->batch_groups = best_g;
+  // ---- single-query path (up to four sample queries, one warm-up pass):
+  // the frontier fraction 1/dense_div at which rounds switch from push to pull
+  std::vector<uint32_t> q1(q_sample, q_sample + std::min<uint32_t>(n_sample, 4));
+  if ((rc = time_single(g, q1, eps, &ms)) != AHPP_OK) return rc;
+  auto tune_single = [&](const char* knob, auto set, const std::vector<uint32_t>& values) -> int {
+    float best = -1.f;
+    uint32_t best_v = values[0];
+    for (uint32_t v : values) {
+      set(v);
+      float t = 0.f;
+      if (int r = time_single(g, q1, eps, &t)) return r;
+      note(knob, v, t / (float)q1.size());
+      if (best < 0.f || t < best) { best = t; best_v = v; }
+    }
+    set(best_v);
+    return AHPP_OK;
+  };
+  const uint32_t saved_div = g->q1_dense_div, saved_vw = g->q1_vw_max;
+  rc = tune_single("single_vec_width", [&](uint32_t v) { g->q1_vw_max = v; }, {32u, 8u, 2u, 1u});
+  if (rc == AHPP_OK)
+    rc = tune_single("single_dense_div", [&](uint32_t v) { g->q1_dense_div = v; }, {32u, 8u, 16u, 64u, 128u});
+  if (rc != AHPP_OK) {
+    g->q1_dense_div = saved_div;
+    g->q1_vw_max = saved_vw;
+    return rc;
+  }
+  g->tune_log = log + "}";
+  return AHPP_OK;
+}
+
+extern "C" int ahpp_autotune_report(const ahpp_graph* g, char* buf, size_t cap, size_t* len) {
+  if (!g) { ahpp::set_error("null graph"); return AHPP_EINVAL; }
+  const std::string& s = g->tune_log;
+  if (len) *len = s.size();
+  if (buf && cap) {
+    const size_t n = std::min(cap - 1, s.size());
+    std::memcpy(buf, s.data(), n);
+    buf[n] = 0;
+  }
   return AHPP_OK;
 }

@@ -1,8 +1,10 @@
 // Batched multi-source push: state and launch parameters.
 //
-// A tile holds kTile queries; every per-node state array of a tile is laid
-// out [node][kTile] (query-minor), so a warp that visits one neighbour reads
-// or writes the 32 queries' values of that neighbour as one 128-byte line.
+// A tile holds 32 (or 16) queries; every per-node state array of a tile is
+// laid out [node][tile] (query-minor), so a warp that visits one neighbour
+// reads or writes the tile's values of that neighbour as one 128-byte (or
+// 64-byte) line.  Buffers are sized for the widest tile (kTile); the kernel
+// instance of a launch's width indexes them with its own width.
 // The graph is streamed once per round per tile, shared by all its queries.
 // `groups` tiles run concurrently, each on its own slice of the persistent
 // grid with its own barrier; a group walks its tiles one after another.
@@ -12,13 +14,19 @@
 
 namespace ahpp {
 
-#ifndef AHPP_TILE
-#define AHPP_TILE 32
-#endif
-constexpr int kTile = AHPP_TILE;   // queries per tile (16 or 32; lane q of a warp-per-node loop = query q)
+constexpr int kTile = 32;          // widest tile (queries per tile); serving uses this width
+constexpr int kTileNarrow = 16;    // the other width of the batched kernel
 constexpr int kRadixBits = 8;      // top-k digit width (per-lane histograms of 256 bins)
 constexpr int kRadixBins = 1 << kRadixBits;
 constexpr int kRadixPasses = 64 / kRadixBits;
+// Block size of the batched kernel (three resident blocks per SM: measured
+// best for this register budget).
+constexpr int kBThreads = 256;
+constexpr int kBWarps = kBThreads / 32;
+constexpr int kBMinBlocks = 3;
+// Dynamic shared memory per block: the top-k radix histograms and sort
+// buffer (4096 keys).
+constexpr size_t kBatchSmem = 32 * 1024;
 
 // Buffers of one concurrent group (one tile in flight).
 struct alignas(64) TileBuf {
@@ -64,6 +72,7 @@ struct BatchParams {
   uint32_t max_rounds = 0;
   uint32_t groups = 1;
   uint32_t dense_div = 32;
+  uint32_t tile = kTile;                   // queries per tile of this launch (kTile or kTileNarrow)
 };
 
 // Per-query control of one batched lane (kept in shared memory while a tile

@@ -28,7 +28,7 @@ namespace ahpp {
 namespace {
 
 constexpr char kMagic[8] = {'A', 'H', 'P', 'P', 'G', 'R', 'F', '1'};
-constexpr uint32_t kVersion = 4;
+constexpr uint32_t kVersion = 5;
 
 struct CacheHeader {
   char magic[8];
@@ -55,6 +55,11 @@ void visit_graph_ptrs(ahpp_graph* g, F f) {
     f((const void**)&L->items);
     f((const void**)&L->split_nchunks);
   }
+  for (int c = 0; c < kChunkChoices; ++c)
+    for (int d = 0; d < 3; ++d) {
+      f((const void**)&G.b_alt[c][d].items);
+      f((const void**)&G.b_alt[c][d].split_nchunks);
+    }
   f((const void**)&g->d_u_new2old);
   f((const void**)&g->d_u_old2new);
 }
@@ -182,8 +187,10 @@ extern "C" int ahpp_load_graph_file(const char* path, const ahpp_config* cfg, ah
     return AHPP_EINVAL;
   }
   if ((c.algo != AHPP_APP && c.algo != AHPP_ASRP) || c.switch_rule < 0 || c.switch_rule > 2 ||
-      (c.batch_tile != 0 && c.batch_tile != 32) || c.batch_groups > (uint32_t)kMaxGroups) {
-    set_error("ahpp_load_graph_file: bad algo, switch_rule, batch_tile or batch_groups");
+      (c.batch_tile != 0 && c.batch_tile != 16 && c.batch_tile != 32) || c.batch_groups > (uint32_t)kMaxGroups ||
+      chunk_choice(c.batch_chunk) < 0 || c.single_vec_width > 32 ||
+      (c.single_vec_width & (c.single_vec_width - 1))) {
+    set_error("ahpp_load_graph_file: bad algo, switch_rule, batch_tile, batch_groups or batch_chunk");
     return AHPP_EINVAL;
   }
   int ndev = 0;
@@ -198,8 +205,9 @@ extern "C" int ahpp_load_graph_file(const char* path, const ahpp_config* cfg, ah
   ahpp_graph* g = new ahpp_graph();
   g->cfg = c;
   g->device = c.device;
-  g->batch_tile = kTile;
+  g->batch_tile = c.batch_tile ? c.batch_tile : (uint32_t)kTile;
   g->batch_groups = c.batch_groups ? c.batch_groups : 1;
+  g->q1_vw_max = c.single_vec_width ? c.single_vec_width : 32;
   g->n_u = h.n_u; g->n_v = h.n_v; g->n_a = h.n_a; g->n_e = h.n_e; g->n_ea = h.n_ea;
   g->bf16 = h.attr_bf16 != 0;
   int rc = AHPP_OK;
@@ -272,6 +280,7 @@ extern "C" int ahpp_load_graph_file(const char* path, const ahpp_config* cfg, ah
       fail(AHPP_ECUDA, "ahpp_load_graph_file: id maps");
     }
   }
+  if (rc == AHPP_OK) select_chunk(g->dg, (uint32_t)chunk_choice(c.batch_chunk));
   if (rc == AHPP_OK) rc = alloc_query_state(g);
   if (rc == AHPP_OK) {
     // lambda: the configured value, else the cached estimate when it was

@@ -198,6 +198,20 @@ HostItems build_units(const std::vector<uint32_t>& deg, uint32_t chunk) {
   return h;
 }
 
+int chunk_choice(uint32_t chunk) {
+  if (chunk == 0) return kChunkDefault;
+  for (int c = 0; c < kChunkChoices; ++c)
+    if (kChunkSizes[c] == chunk) return c;
+  return -1;
+}
+
+void select_chunk(DevGraph& G, uint32_t choice) {
+  G.b_chunk = choice;
+  G.b_v = G.b_alt[choice][0];
+  G.b_a = G.b_alt[choice][1];
+  G.b_u = G.b_alt[choice][2];
+}
+
 int build_graph(const ahpp_graph_desc* d, ahpp_graph* g) {
   const ahpp_config& cfg = g->cfg;
   const uint64_t lim = (1ull << 31) - 1;
@@ -324,13 +338,13 @@ int build_graph(const ahpp_graph_desc* d, ahpp_graph* g) {
   for (uint32_t v = 0; v < nV; ++v) dg_v[v] = vu_off[v + 1] - vu_off[v];
   for (uint32_t a = 0; a < nA; ++a) dg_a[a] = au_off[a + 1] - au_off[a];
   const ItemShape s1{64, 32, 0xffffffffu, 2048};
-#ifndef AHPP_UNIT_CHUNK
-#define AHPP_UNIT_CHUNK 256   // entries per chunk of a long row in the batched pull phases
-#endif
-  const uint32_t kUnitChunk = AHPP_UNIT_CHUNK;
   HostItems i1v = build_items(dg_v, s1), i1a = build_items(dg_a, s1), i1u = build_items(dg_u, s1);
-  HostItems ibv = build_units(dg_v, kUnitChunk), iba = build_units(dg_a, kUnitChunk),
-            ibu = build_units(dg_u, kUnitChunk);
+  std::vector<HostItems> ib;
+  for (int c = 0; c < kChunkChoices; ++c) {
+    ib.push_back(build_units(dg_v, kChunkSizes[c]));
+    ib.push_back(build_units(dg_a, kChunkSizes[c]));
+    ib.push_back(build_units(dg_u, kChunkSizes[c]));
+  }
 
   // 6. upload
   auto up = [&](const void* src, size_t bytes) -> void* {
@@ -378,7 +392,13 @@ int build_graph(const ahpp_graph_desc* d, ahpp_graph* g) {
     L.n_long = h.n_long;
   };
   up_items(i1v, G.s1_v); up_items(i1a, G.s1_a); up_items(i1u, G.s1_u);
-  up_items(ibv, G.b_v); up_items(iba, G.b_a); up_items(ibu, G.b_u);
+  G.b_split_max = 0;
+  for (int c = 0; c < kChunkChoices; ++c) {
+    for (int d = 0; d < 3; ++d) up_items(ib[3 * c + d], G.b_alt[c][d]);
+    G.b_split_max = std::max(G.b_split_max,
+                             G.b_alt[c][0].n_split + G.b_alt[c][1].n_split + G.b_alt[c][2].n_split);
+  }
+  select_chunk(G, kChunkDefault);
 
   g->h_u_old2new = u_o2n;
   g->h_u_new2old = u_n2o;
@@ -392,6 +412,19 @@ int build_graph(const ahpp_graph_desc* d, ahpp_graph* g) {
   g->graph_bytes = 0;
   for (auto& b : g->bufs) g->graph_bytes += b.bytes;
   return alloc_query_state(g);
+}
+
+// Shared-memory plan of the single-query kernel's pull rounds: phase 2
+// holds t_A and, with the attribute push, its accumulator over A when both
+// fit in kQ1AttrSmem.  Shared memory not planned here stays L1.
+void plan_query1_smem(ahpp_graph* g) {
+  constexpr uint64_t kQ1AttrSmem = 96 * 1024;
+  const DevGraph& G = g->dg;
+  const uint32_t smax = query1_max_smem(g->device);
+  const uint64_t na4 = 4ull * G.n_a;
+  g->q1_attr_push = 2 * na4 <= std::min<uint64_t>(kQ1AttrSmem, smax);
+  g->q1_ta_smem = g->q1_attr_push;
+  g->q1_smem = g->q1_attr_push ? (uint32_t)((2 * na4 + 15) / 16 * 16) : 0u;
 }
 
 // Single-query state of a loaded graph (working vectors, lists, accumulators,
@@ -408,6 +441,7 @@ int alloc_query_state(ahpp_graph* g) {
   s.pic = (float*)g->alloc(4ull * nU);
   s.t_v = (float*)g->alloc(4ull * std::max(nV, 1u));
   s.t_a = (float*)g->alloc(4ull * std::max(nA, 1u));
+  s.t_a2 = (float*)g->alloc(4ull * std::max(nA, 1u));
   s.list_u = (uint32_t*)g->alloc(4ull * nU);
   s.list_v = (uint32_t*)g->alloc(4ull * std::max(nV, 1u));
   s.list_a = (uint32_t*)g->alloc(4ull * std::max(nA, 1u));
@@ -428,8 +462,11 @@ int alloc_query_state(ahpp_graph* g) {
   AHPP_CUDA(cudaMemset(s.bar, 0, sizeof(GridBarrier)));
   AHPP_CUDA(cudaMemset(s.split_acc, 0, 4ull * std::max(g->n_split1, 1u)));
   AHPP_CUDA(cudaMemset(s.split_cnt, 0, 4ull * std::max(g->n_split1, 1u)));
-  g->q1_grid = query1_max_grid(g->bf16, g->sm_count);
+  plan_query1_smem(g);
+  g->q1_grid = query1_max_grid(g->bf16, g->sm_count, g->q1_smem);
   if (g->q1_grid <= 0) { set_error("ahpp_load_graph: occupancy query failed"); return AHPP_ECUDA; }
+  BatchParams plan;
+  if (int rc = batch_plan(g, plan)) return rc;
   if (cfg.hbm_budget_bytes && g->graph_bytes + g->q1_bytes > cfg.hbm_budget_bytes) {
     set_error("ahpp_load_graph: graph and query state exceed hbm_budget_bytes");
     return AHPP_ENOMEM;

@@ -94,6 +94,12 @@ struct ahpp_graph {
   // single-query state
   ahpp::Q1State q1{};
   int q1_grid = 0;
+  // single-query kernel's shared-memory plan (see Q1Params)
+  uint32_t q1_smem = 0;
+  int q1_attr_push = 0, q1_ta_smem = 0;
+  uint32_t q1_dense_div = 32;     // pull rounds once the frontier covers > 1/dense_div of the edges
+  uint32_t q1_vw_max = 32;        // lanes per short row in the pull phases (at most)
+  std::string tune_log;           // the last autotune's measurements (JSON object)
   uint32_t n_split1 = 0;
   uint64_t q1_bytes = 0;
 
@@ -126,12 +132,22 @@ int reset_barrier(ahpp_graph* g, GridBarrier* bar, cudaStream_t stream, bool kee
 // Synchronous (reads one word from the device on `stream`).
 int barrier_status(GridBarrier* bar, cudaStream_t stream, int* status);
 int build_graph(const ahpp_graph_desc* desc, ahpp_graph* g);
+// Shared-memory plan of the single-query kernel (the grid does not depend on
+// it: one block per SM).
+void plan_query1_smem(ahpp_graph* g);
+// Index into kChunkSizes of a configured chunk size (0: the default), -1 if
+// it is not one of them.
+int chunk_choice(uint32_t chunk);
+// Make chunk choice `choice` (index into kChunkSizes) the active unit lists.
+void select_chunk(DevGraph& G, uint32_t choice);
 int alloc_query_state(ahpp_graph* g);
 int run_lambda(ahpp_graph* g);
 int run_query1(ahpp_graph* g, uint32_t q_new, double eps, uint32_t lambda_T_mode,
                cudaStream_t stream, QCtl* h_ctl);
 int topk_single(ahpp_graph* g, const float* d_score, uint32_t k, uint32_t* d_nodes,
                 float* d_scores, uint32_t* d_n, cudaStream_t stream);
+// The batched kernel's grid (computed once per graph).
+int batch_plan(ahpp_graph* g, BatchParams& p);
 int run_single_device(ahpp_graph* g, uint32_t q, double eps, uint32_t k, uint32_t* d_out_nodes,
                       float* d_out_scores, uint32_t* d_out_n, ahpp_stats* d_stats, cudaStream_t s);
 }  // namespace ahpp

@@ -32,6 +32,11 @@ constexpr int kWarps = kThreads / 32;
 constexpr uint32_t kItemLong = 0x40000000u;   // item = one whole long row (warp-cooperative)
 constexpr uint32_t kItemSplit = 0x80000000u;  // item = one chunk of a split row (| slot)
 constexpr uint32_t kItemMask = 0x3fffffffu;
+// Entries per chunk of a long row in the batched pull phases: the unit lists
+// of every choice are built at load, ahpp_autotune picks one (default 256).
+constexpr int kChunkChoices = 3;
+constexpr uint32_t kChunkSizes[kChunkChoices] = {128, 256, 512};
+constexpr int kChunkDefault = 1;
 
 // Work items of a pull sweep over one row space.
 //   x = first row; y = number of rows (short group, one row per lane) or a flag;
@@ -63,8 +68,12 @@ struct DevGraph {
   float k_attr = 0.f;                   // (1 - alpha) * beta
   // single-query (one row per lane / warp-cooperative) work items
   ItemList s1_v, s1_a, s1_u;
-  // batched row-group units
+  // batched row-group units (the active chunk size) and those of every chunk
+  // choice (kChunkSizes); b_split_max = the most split slots of any choice
   ItemList b_v, b_a, b_u;
+  ItemList b_alt[kChunkChoices][3];
+  uint32_t b_chunk = kChunkDefault;
+  uint32_t b_split_max = 0;
 };
 
 template <typename WA>
@@ -239,12 +248,14 @@ struct Partials {
   double sum_r = 0.0;
 };
 
-// Block reduction of Partials into acc (one atomic per field per block).
+// Block reduction of Partials into acc (one atomic per field per block);
+// NW = warps per block.
+template <int NW>
 __device__ __forceinline__ void flush_partials(Partials& p, RAcc* acc) {
-  __shared__ float s_max[kWarps];
-  __shared__ uint32_t s_marked[kWarps];
-  __shared__ unsigned long long s_deg[kWarps], s_np[kWarps];
-  __shared__ double s_sum[kWarps];
+  __shared__ float s_max[NW];
+  __shared__ uint32_t s_marked[NW];
+  __shared__ unsigned long long s_deg[NW], s_np[NW];
+  __shared__ double s_sum[NW];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   float m = warp_max(p.max_r);
   uint32_t mk = warp_sum_u32(p.marked);
@@ -254,7 +265,7 @@ __device__ __forceinline__ void flush_partials(Partials& p, RAcc* acc) {
   if (lane == 0) { s_max[warp] = m; s_marked[warp] = mk; s_deg[warp] = dg; s_np[warp] = np; s_sum[warp] = sm; }
   __syncthreads();
   if (threadIdx.x == 0) {
-    for (int w = 1; w < kWarps; ++w) {
+    for (int w = 1; w < NW; ++w) {
       m = fmaxf(m, s_max[w]); mk += s_marked[w]; dg += s_deg[w]; np += s_np[w]; sm += s_sum[w];
     }
     if (m > 0.f) atomicMax(&acc->max_r_bits, __float_as_uint(m));

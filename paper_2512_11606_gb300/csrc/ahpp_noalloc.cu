@@ -60,6 +60,7 @@ size_t carve(const ahpp_graph* g, char* base, Q1State* s) {
   s->pic = (float*)take(4 * nu);
   s->t_v = (float*)take(4 * nv);
   s->t_a = (float*)take(4 * na);
+  s->t_a2 = (float*)take(4 * na);
   s->list_u = (uint32_t*)take(4 * nu);
   s->list_v = (uint32_t*)take(4 * nv);
   s->list_a = (uint32_t*)take(4 * na);

@@ -44,30 +44,110 @@ struct Ctx {
   uint32_t gt, nt;     // global thread id / count
 };
 
-__device__ __forceinline__ float pushed(const float* r_u, uint32_t u) {
-  return fmaxf(-r_u[u], 0.f);
-}
-
 // ---------------------------------------------------------------- phase 1
-// t_V[v] = sum_u c_uv p_u ;  t_A[a] = k_attr cnorm_a[a] sum_u w(u,a) rnorm_u[u] p_u
+// t_V[v] = sum_u c_uv p_u ;  t_A[a] = k_attr cnorm_a[a] sum_u (w(u,a) rnorm_u[u]) p_u
+// (the A->U pull coefficient w(u,a) rnorm_u[u] is precomputed per entry).
 
-__device__ __forceinline__ void p1_epilogue(const Ctx& c, bool is_a, uint32_t row, float s,
+__device__ __forceinline__ void p1_epilogue(const Ctx& c, bool is_a, uint32_t row, float s, float* ta_out,
                                             Partials& part) {
   if (!is_a) {
     c.s.t_v[row] = s;
     if (s > 0.f) part.np_flush += c.g.vu_off[row + 1] - c.g.vu_off[row];
   } else {
     float t = c.g.k_attr * c.g.cnorm_a[row] * s;
-    c.s.t_a[row] = t;
+    ta_out[row] = t;
     if (t > 0.f) part.np_flush += c.g.au_off[row + 1] - c.g.au_off[row];
   }
 }
 
+// sum_k coef[k] * x(idx[k]) over a warp's share of a long row: lane l takes entries
+// z + l, z + l + 32, ... (two per step).
+template <typename CoefF, typename XF>
+__device__ __forceinline__ float lane_dot(uint32_t z, uint32_t w, uint32_t lane, const uint32_t* __restrict__ idx,
+                                          CoefF coef, XF x, float s) {
+  uint32_t k = z + lane;
+  for (; k + 32 < w; k += 64) {
+    const uint32_t i0 = idx[k], i1 = idx[k + 32];
+    const float c0 = coef(k), c1 = coef(k + 32);
+    const float x0 = x(i0), x1 = x(i1);
+    s = fmaf(c0, x0, s);
+    s = fmaf(c1, x1, s);
+  }
+  if (k < w) s = fmaf(coef(k), x(idx[k]), s);
+  return s;
+}
+
+// Lanes per row for an item of nr short rows holding nnz entries: the mean
+// row length rounded up to a power of two, at most vw_max (a power of two
+// <= 32).  Rows are sorted by degree, so an item's rows have about that
+// length; vw lanes then walk each row together and one load of the warp
+// reads contiguous entries.
+__device__ __forceinline__ uint32_t vec_width(uint32_t nnz, uint32_t nr, uint32_t vw_max) {
+  const uint32_t mean = (nnz + nr - 1) / max(nr, 1u);
+  return mean <= 1 ? 1u : min(vw_max, 1u << (32 - __clz(mean - 1)));
+}
+
+// Sum over the vw lanes of a row's segment (every lane of the warp calls it).
+__device__ __forceinline__ float seg_sum(float s, uint32_t vw) {
+  for (uint32_t o = vw >> 1; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  return s;
+}
+
+// sum over k = b, b + vw, b + 2 vw, ... < e of coef(k) x(idx[k]), four
+// entries per step (their loads are in flight together); returns the sum and
+// leaves k at the first index >= e of the sequence.
+template <typename CoefF, typename XF>
+__device__ __forceinline__ float strided_dot(uint32_t& k, uint32_t e, uint32_t vw, const uint32_t* __restrict__ idx,
+                                             CoefF coef, XF x, float s) {
+  for (; k + 3 * vw < e; k += 4 * vw) {
+    const uint32_t i0 = idx[k], i1 = idx[k + vw], i2 = idx[k + 2 * vw], i3 = idx[k + 3 * vw];
+    const float c0 = coef(k), c1 = coef(k + vw), c2 = coef(k + 2 * vw), c3 = coef(k + 3 * vw);
+    const float x0 = x(i0), x1 = x(i1), x2 = x(i2), x3 = x(i3);
+    s = fmaf(c0, x0, s);
+    s = fmaf(c1, x1, s);
+    s = fmaf(c2, x2, s);
+    s = fmaf(c3, x3, s);
+  }
+  for (; k < e; k += vw) s = fmaf(coef(k), x(idx[k]), s);
+  return s;
+}
+
+// Rows 0..nr-1 (nr <= 32) of an item, vw lanes per row: part(r, sub) is lane
+// sub's share of row r; returns row `lane`'s total in lane `lane` (0 for
+// lanes >= nr).  Passes of 32 / vw rows; after pass p the sums of its rows
+// sit in lanes 0, vw, 2 vw, ... and move to lanes p (32 / vw) + 0, 1, ...
+template <typename PartF>
+__device__ __forceinline__ float rows_to_lanes(uint32_t nr, uint32_t vw, uint32_t lane, PartF part) {
+  const uint32_t sub = lane & (vw - 1), rpp = 32 / vw, npass = (nr + rpp - 1) / rpp;
+  float mine = 0.f;
+  for (uint32_t pass = 0; pass < npass; ++pass) {        // warp-uniform
+    const uint32_t r = pass * rpp + lane / vw;
+    float s = r < nr ? part(r, sub) : 0.f;
+    s = seg_sum(s, vw);
+    const float t = __shfl_sync(0xffffffffu, s, (lane % rpp) * vw);
+    if (lane / rpp == pass) mine = t;
+  }
+  return mine;
+}
+
 template <typename WA>
-__device__ void phase1(const Ctx& c, Partials& part) {
+__device__ void phase1(const Ctx& c, Partials& part, bool do_a, float* ta_out, const float* ta_scan,
+                       float* ta_zero) {
   const DevGraph& g = c.g;
   const uint32_t lane = lane_id();
-  const uint32_t nv = g.s1_v.n_items, total = nv + g.s1_a.n_items;
+  if (ta_scan || ta_zero) {
+    // t_A of this round was pushed by the previous phase 2: count its active
+    // attributes (Algorithm 4's push counter) and clear the next round's buffer
+    for (uint32_t a = c.gt; a < g.n_a; a += c.nt) {
+      if (ta_scan && ta_scan[a] > 0.f) part.np_flush += g.au_off[a + 1] - g.au_off[a];
+      if (ta_zero) ta_zero[a] = 0.f;
+    }
+  }
+  const float* __restrict__ r_u = c.s.r_u;
+  auto P = [&](uint32_t u) { return fmaxf(-r_u[u], 0.f); };
+  auto cv = [&](uint32_t k) { return g.vu_c[k]; };
+  auto ca = [&](uint32_t k) { return g.au_c[k]; };
+  const uint32_t nv = g.s1_v.n_items, total = nv + (do_a ? g.s1_a.n_items : 0u);
   for (uint32_t it = c.gw; it < total; it += c.nw) {
     const bool is_a = it >= nv;
     const uint4 item = is_a ? g.s1_a.items[it - nv] : g.s1_v.items[it];
@@ -75,18 +155,8 @@ __device__ void phase1(const Ctx& c, Partials& part) {
     const uint32_t* idx = is_a ? g.au_idx : g.vu_idx;
     if (item.y & (kItemLong | kItemSplit)) {
       const uint32_t row = item.x, base = off[row];
-      float s = 0.f;
-      if (!is_a) {
-        for (uint32_t k = item.z + lane; k < item.w; k += 32) {
-          uint32_t u = idx[base + k];
-          s = fmaf(g.vu_c[base + k], pushed(c.s.r_u, u), s);
-        }
-      } else {
-        for (uint32_t k = item.z + lane; k < item.w; k += 32) {
-          uint32_t u = idx[base + k];
-          s = fmaf(wload<WA>(g.au_w, base + k) * g.rnorm_u[u], pushed(c.s.r_u, u), s);
-        }
-      }
+      float s = is_a ? lane_dot(base + item.z, base + item.w, lane, idx, ca, P, 0.f)
+                     : lane_dot(base + item.z, base + item.w, lane, idx, cv, P, 0.f);
       s = warp_sum(s);
       if (lane == 0) {
         if (item.y & kItemSplit) {
@@ -98,35 +168,37 @@ __device__ void phase1(const Ctx& c, Partials& part) {
           if (atomicAdd(&c.s.split_cnt[slot], 1u) == nch - 1) {
             float tot = atomicExch(&c.s.split_acc[slot], 0.f);
             c.s.split_cnt[slot] = 0;
-            p1_epilogue(c, is_a, row, tot, part);
+            p1_epilogue(c, is_a, row, tot, ta_out, part);
           }
         } else {
-          p1_epilogue(c, is_a, row, s, part);
+          p1_epilogue(c, is_a, row, s, ta_out, part);
         }
       }
-    } else if (lane < item.y) {
-      const uint32_t row = item.x + lane;
-      const uint32_t b = off[row], e = off[row + 1];
-      float s = 0.f;
-      if (!is_a) {
-        for (uint32_t k = b; k < e; ++k) s = fmaf(g.vu_c[k], pushed(c.s.r_u, idx[k]), s);
-      } else {
-        for (uint32_t k = b; k < e; ++k) {
-          uint32_t u = idx[k];
-          s = fmaf(wload<WA>(g.au_w, k) * g.rnorm_u[u], pushed(c.s.r_u, u), s);
-        }
-      }
-      p1_epilogue(c, is_a, row, s, part);
+    } else {
+      // up to 32 short rows: vw lanes walk each row (coalesced loads), then
+      // lane r holds row r's sum and the epilogues run one row per lane
+      const uint32_t r0 = item.x, nr = item.y;
+      const uint32_t vw = vec_width(off[r0 + nr] - off[r0], nr, c.p.vw_max);
+      const float mine = rows_to_lanes(nr, vw, lane, [&](uint32_t r, uint32_t sub) {
+        uint32_t k = off[r0 + r] + sub;
+        const uint32_t e = off[r0 + r + 1];
+        return is_a ? strided_dot(k, e, vw, idx, ca, P, 0.f) : strided_dot(k, e, vw, idx, cv, P, 0.f);
+      });
+      if (lane < nr) p1_epilogue(c, is_a, r0 + lane, mine, ta_out, part);
     }
   }
 }
 
 // ---------------------------------------------------------------- phase 2
 // r_U'[u] = kept_u + sum_v w(u,v) t_V[v] + sum_a w(u,a) t_A[a]; reserve update of
-// the nodes pushed this round; marking of the next frontier with threshold th.
+// the nodes pushed this round; marking of the next frontier with threshold th;
+// with the attribute push, the marked node's attribute share of the next
+// round: acc[a] += w(u,a) rnorm_u[u] p_u (block-local, shared memory), added
+// to t_A' scaled by k_attr cnorm_a[a] at the end of the phase.
 
-__device__ __forceinline__ void p2_epilogue(const Ctx& c, uint32_t u, float s, uint32_t cnt,
-                                            double theta, bool per_node, Partials& part) {
+// Returns the residue marked for the next push (0 if u is not marked).
+__device__ __forceinline__ float p2_epilogue(const Ctx& c, uint32_t u, float s, uint32_t cnt,
+                                             double theta, bool per_node, Partials& part) {
   float r_old = c.s.r_u[u];
   float kept = r_old;
   if (r_old < 0.f) {
@@ -148,15 +220,40 @@ __device__ __forceinline__ void p2_epilogue(const Ctx& c, uint32_t u, float s, u
     c.s.r_u[u] = -r_new;
     part.marked += 1;
     part.marked_deg += cnt;
-  } else {
-    c.s.r_u[u] = r_new;
+    return r_new;
   }
+  c.s.r_u[u] = r_new;
+  return 0.f;
 }
 
 template <typename WA>
-__device__ void phase2(const Ctx& c, double theta, bool per_node, Partials& part) {
+__device__ __forceinline__ void push_attr_smem(const DevGraph& g, uint32_t u, float p, float* acc) {
+  const uint32_t b = g.ua_off[u], e = g.ua_off[u + 1];
+  const float f = g.rnorm_u[u] * p;
+  for (uint32_t k = b; k < e; ++k) atomicAdd(&acc[g.ua_idx[k]], wload<WA>(g.ua_w, k) * f);
+}
+
+template <typename WA>
+__device__ void phase2(const Ctx& c, double theta, bool per_node, Partials& part, const float* ta_cur,
+                       float* ta_next, float* smem) {
   const DevGraph& g = c.g;
   const uint32_t lane = lane_id();
+  const uint32_t na = g.n_a;
+  // shared memory (ta_smem): a copy of t_A and, with the push, its accumulator
+  float* s_ta = smem;
+  float* s_acc = smem + na;
+  if (c.p.ta_smem) {
+    for (uint32_t a = threadIdx.x; a < na; a += blockDim.x) {
+      s_ta[a] = ta_cur[a];
+      if (ta_next) s_acc[a] = 0.f;
+    }
+    __syncthreads();
+  }
+  const float* __restrict__ t_v = c.s.t_v;
+  auto TV = [&](uint32_t v) { return t_v[v]; };
+  auto TA = [&](uint32_t a) { return c.p.ta_smem ? s_ta[a] : ta_cur[a]; };
+  auto wv = [&](uint32_t k) { return g.uv_w[k]; };
+  auto wa = [&](uint32_t k) { return wload<WA>(g.ua_w, k); };
   const uint32_t total = g.s1_u.n_items;
   for (uint32_t it = c.gw; it < total; it += c.nw) {
     const uint4 item = g.s1_u.items[it];
@@ -164,16 +261,13 @@ __device__ void phase2(const Ctx& c, double theta, bool per_node, Partials& part
       const uint32_t u = item.x;
       const uint32_t b1 = g.uv_off[u], dv = g.uv_off[u + 1] - b1;
       const uint32_t b2 = g.ua_off[u], da = g.ua_off[u + 1] - b2;
+      // chunk [z, w) of the combined list: V neighbours first, then attributes
       float s = 0.f;
-      for (uint32_t k = item.z + lane; k < item.w; k += 32) {
-        if (k < dv) {
-          s = fmaf(g.uv_w[b1 + k], c.s.t_v[g.uv_idx[b1 + k]], s);
-        } else {
-          uint32_t j = b2 + (k - dv);
-          s = fmaf(wload<WA>(g.ua_w, j), c.s.t_a[g.ua_idx[j]], s);
-        }
-      }
+      if (item.z < dv) s = lane_dot(b1 + item.z, b1 + min(item.w, dv), lane, g.uv_idx, wv, TV, s);
+      if (item.w > dv) s = lane_dot(b2 + (item.z > dv ? item.z - dv : 0), b2 + (item.w - dv), lane, g.ua_idx, wa,
+                                    TA, s);
       s = warp_sum(s);
+      float pm = 0.f;
       if (lane == 0) {
         if (item.y & kItemSplit) {
           const uint32_t slot = (item.y & kItemMask) + g.s1_v.n_split + g.s1_a.n_split;
@@ -183,20 +277,43 @@ __device__ void phase2(const Ctx& c, double theta, bool per_node, Partials& part
           if (atomicAdd(&c.s.split_cnt[slot], 1u) == nch - 1) {
             float tot = atomicExch(&c.s.split_acc[slot], 0.f);
             c.s.split_cnt[slot] = 0;
-            p2_epilogue(c, u, tot, dv + da, theta, per_node, part);
+            pm = p2_epilogue(c, u, tot, dv + da, theta, per_node, part);
           }
         } else {
-          p2_epilogue(c, u, s, dv + da, theta, per_node, part);
+          pm = p2_epilogue(c, u, s, dv + da, theta, per_node, part);
         }
+        if (ta_next && pm > 0.f) push_attr_smem<WA>(g, u, pm, s_acc);
       }
-    } else if (lane < item.y) {
-      const uint32_t u = item.x + lane;
-      const uint32_t b1 = g.uv_off[u], e1 = g.uv_off[u + 1];
-      const uint32_t b2 = g.ua_off[u], e2 = g.ua_off[u + 1];
-      float s = 0.f;
-      for (uint32_t k = b1; k < e1; ++k) s = fmaf(g.uv_w[k], c.s.t_v[g.uv_idx[k]], s);
-      for (uint32_t k = b2; k < e2; ++k) s = fmaf(wload<WA>(g.ua_w, k), c.s.t_a[g.ua_idx[k]], s);
-      p2_epilogue(c, u, s, (e1 - b1) + (e2 - b2), theta, per_node, part);
+    } else {
+      // up to 32 short rows (V neighbours, then attributes): vw lanes walk each
+      // row, then the epilogues and attribute pushes run one row per lane
+      const uint32_t u0 = item.x, nr = item.y;
+      const uint32_t nnz = (g.uv_off[u0 + nr] - g.uv_off[u0]) + (g.ua_off[u0 + nr] - g.ua_off[u0]);
+      const uint32_t vw = vec_width(nnz, nr, c.p.vw_max);
+      const float mine = rows_to_lanes(nr, vw, lane, [&](uint32_t r, uint32_t sub) {
+        // lane sub takes entries sub, sub + vw, ... of the combined list:
+        // the V neighbours [0, dv), then the attributes [dv, dv + da)
+        const uint32_t u = u0 + r;
+        const uint32_t b1 = g.uv_off[u], dv = g.uv_off[u + 1] - b1;
+        const uint32_t b2 = g.ua_off[u], da = g.ua_off[u + 1] - b2;
+        uint32_t k = b1 + sub;
+        float s = strided_dot(k, b1 + dv, vw, g.uv_idx, wv, TV, 0.f);
+        k = k - b1 - dv + b2;              // the same lane's first attribute entry
+        return strided_dot(k, b2 + da, vw, g.ua_idx, wa, TA, s);
+      });
+      if (lane < nr) {
+        const uint32_t u = u0 + lane;
+        const uint32_t cnt = (g.uv_off[u + 1] - g.uv_off[u]) + (g.ua_off[u + 1] - g.ua_off[u]);
+        const float pm = p2_epilogue(c, u, mine, cnt, theta, per_node, part);
+        if (ta_next && pm > 0.f) push_attr_smem<WA>(g, u, pm, s_acc);
+      }
+    }
+  }
+  if (ta_next) {
+    __syncthreads();
+    for (uint32_t a = threadIdx.x; a < na; a += blockDim.x) {
+      const float v = s_acc[a];
+      if (v != 0.f) atomicAdd(&ta_next[a], g.k_attr * g.cnorm_a[a] * v);
     }
   }
 }
@@ -334,11 +451,12 @@ __device__ __forceinline__ double budget_of(const Q1Params& p, double M) {
 }  // namespace
 
 template <typename WA>
-__global__ void __launch_bounds__(kThreads)
+__global__ void __launch_bounds__(kQ1Threads, 1)
 k_query1(const __grid_constant__ DevGraph g, const __grid_constant__ Q1State s,
          const __grid_constant__ Q1Params p) {
-  Ctx c{g, s, p, (blockIdx.x * kThreads + threadIdx.x) >> 5, (gridDim.x * kThreads) >> 5,
-        blockIdx.x * kThreads + threadIdx.x, gridDim.x * kThreads};
+  extern __shared__ __align__(16) float q1_smem[];
+  Ctx c{g, s, p, (blockIdx.x * kQ1Threads + threadIdx.x) >> 5, (gridDim.x * kQ1Threads) >> 5,
+        blockIdx.x * kQ1Threads + threadIdx.x, gridDim.x * kQ1Threads};
   const bool leader = blockIdx.x == 0 && threadIdx.x == 0;
   const unsigned int nb = gridDim.x;
   const bool app = p.algo == kAlgoAPP;
@@ -347,7 +465,7 @@ k_query1(const __grid_constant__ DevGraph g, const __grid_constant__ Q1State s,
   const float r0 = p.lambda_mode ? -1.f : 0.f;
   for (uint32_t u = c.gt; u < g.n_u; u += c.nt) { s.r_u[u] = r0; s.pi[u] = 0.f; s.pic[u] = 0.f; }
   for (uint32_t v = c.gt; v < g.n_v; v += c.nt) s.t_v[v] = 0.f;
-  for (uint32_t a = c.gt; a < g.n_a; a += c.nt) s.t_a[a] = 0.f;
+  for (uint32_t a = c.gt; a < g.n_a; a += c.nt) { s.t_a[a] = 0.f; s.t_a2[a] = 0.f; }
   for (uint32_t i = c.gt; i < p.n_split; i += c.nt) { s.split_acc[i] = 0.f; s.split_cnt[i] = 0; }
   if (c.gt < 3) s.racc[c.gt] = RAcc{};
   if (leader) {
@@ -386,6 +504,12 @@ k_query1(const __grid_constant__ DevGraph g, const __grid_constant__ Q1State s,
   uint32_t rounds = 0, switch_round = 0, dense_rounds = 0;
   unsigned long long n_p = 0, pushes = 0;
   Partials part;
+  // attribute push: t_A of a pull round lives in ta_buf[ta_sel] and phase 2
+  // pushes the next round's into the other buffer; the first pull round, and
+  // the round after the ASRP switch marks more nodes, pull t_A instead
+  float* const ta_buf[2] = {s.t_a, s.t_a2};
+  int ta_sel = 0;
+  bool pull_a = true;
 
   for (; status == kStatusOk;) {
     RAcc* A = &s.racc[rounds % 3];
@@ -405,15 +529,20 @@ k_query1(const __grid_constant__ DevGraph g, const __grid_constant__ Q1State s,
       if (!grid_sync(s.bar, nb)) { status = kStatusWait; break; }
       const uint32_t nv = __ldcg(&A->n_list_v), na = __ldcg(&A->n_list_a);
       flush_va<WA>(c, nv, na, part);
-      flush_partials(part, A);
+      flush_partials<kQ1Warps>(part, A);
       if (!grid_sync(s.bar, nb)) { status = kStatusWait; break; }
     } else {
-      phase1<WA>(c, part);
-      flush_partials(part, A);
+      float* ta_cur = ta_buf[ta_sel];
+      float* ta_next = p.attr_push ? ta_buf[ta_sel ^ 1] : nullptr;
+      const bool do_a = !p.attr_push || pull_a;
+      phase1<WA>(c, part, do_a, ta_cur, do_a ? nullptr : ta_cur, ta_next);
+      flush_partials<kQ1Warps>(part, A);
       if (!grid_sync(s.bar, nb)) { status = kStatusWait; break; }
-      phase2<WA>(c, theta, app, part);
-      flush_partials(part, A);
+      phase2<WA>(c, theta, app, part, ta_cur, ta_next, q1_smem);
+      flush_partials<kQ1Warps>(part, A);
       if (!grid_sync(s.bar, nb)) { status = kStatusWait; break; }
+      if (p.attr_push) ta_sel ^= 1;
+      pull_a = false;
       ++dense_rounds;
     }
     ++rounds;
@@ -436,12 +565,13 @@ k_query1(const __grid_constant__ DevGraph g, const __grid_constant__ Q1State s,
     if (!dense) {
       const double th_next = app ? p.eps_f : (phase == kPhaseSync ? 0.0 : p.eps_f);
       select_frontier(c, th_next, app, A, part);
-      flush_partials(part, A);
+      flush_partials<kQ1Warps>(part, A);
       if (!grid_sync(s.bar, nb)) { status = kStatusWait; break; }
     } else if (switched) {
       mark_remaining(c, part);
-      flush_partials(part, A);
+      flush_partials<kQ1Warps>(part, A);
       if (!grid_sync(s.bar, nb)) { status = kStatusWait; break; }
+      pull_a = true;       // the new marks did not push their attribute share
     }
   }
 
@@ -482,26 +612,61 @@ template __global__ void k_query1<__nv_bfloat16>(const __grid_constant__ DevGrap
                                                  const __grid_constant__ Q1State,
                                                  const __grid_constant__ Q1Params);
 
-// Launch helper: persistent cooperative grid sized to full residency.
+// Launch helper: persistent cooperative grid (one block per SM).
+namespace {
+const void* q1_fn(bool bf16) {
+  return bf16 ? (const void*)k_query1<__nv_bfloat16> : (const void*)k_query1<float>;
+}
+}  // namespace
+
+void prefer_l1(bool bf16) {
+  static bool done[2] = {false, false};
+  if (!done[bf16]) {
+    // only the planned shared memory is carved out; the rest stays L1, which
+    // holds the lines of the rows the lanes are walking
+    cudaFuncSetAttribute(q1_fn(bf16), cudaFuncAttributePreferredSharedMemoryCarveout,
+                         (int)cudaSharedmemCarveoutMaxL1);
+    done[bf16] = true;
+  }
+}
+
+uint32_t query1_max_smem(int device) {
+  int optin = 0;
+  if (cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, device) != cudaSuccess) {
+    cudaGetLastError();
+    return 0;
+  }
+  cudaFuncAttributes fa{};
+  if (cudaFuncGetAttributes(&fa, q1_fn(true)) != cudaSuccess) {
+    cudaGetLastError();
+    return 0;
+  }
+  const long room = (long)optin - (long)fa.sharedSizeBytes - 1024;   // static shared memory + margin
+  return room > 0 ? (uint32_t)(room / 16 * 16) : 0u;
+}
+
 int launch_query1(const DevGraph& g, const Q1State& s, const Q1Params& p, bool bf16,
                   int grid, cudaStream_t stream) {
   void* args[] = {(void*)&g, (void*)&s, (void*)&p};
-  cudaError_t e;
-  if (bf16)
-    e = cudaLaunchCooperativeKernel((const void*)k_query1<__nv_bfloat16>, dim3(grid),
-                                    dim3(kThreads), args, 0, stream);
-  else
-    e = cudaLaunchCooperativeKernel((const void*)k_query1<float>, dim3(grid), dim3(kThreads),
-                                    args, 0, stream);
+  prefer_l1(bf16);
+  cudaError_t e = cudaFuncSetAttribute(q1_fn(bf16), cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)p.smem_bytes);
+  if (e == cudaSuccess)
+    e = cudaLaunchCooperativeKernel(q1_fn(bf16), dim3(grid), dim3(kQ1Threads), args, p.smem_bytes, stream);
   return e == cudaSuccess ? 0 : (int)e;
 }
 
-int query1_max_grid(bool bf16, int sm_count) {
+int query1_max_grid(bool bf16, int sm_count, uint32_t smem_bytes) {
   int per_sm = 0;
-  cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-      &per_sm, bf16 ? (const void*)k_query1<__nv_bfloat16> : (const void*)k_query1<float>,
-      kThreads, 0);
-  if (e != cudaSuccess || per_sm <= 0) return -1;
+  prefer_l1(bf16);
+  cudaError_t e = cudaFuncSetAttribute(q1_fn(bf16), cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)smem_bytes);
+  if (e == cudaSuccess)
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, q1_fn(bf16), kQ1Threads, smem_bytes);
+  if (e != cudaSuccess || per_sm <= 0) {
+    cudaGetLastError();
+    return -1;
+  }
   return per_sm * sm_count;
 }
 

@@ -5,9 +5,15 @@
 namespace ahpp {
 
 // Device state of one query (all arrays indexed by internal ids).
+// Block size of the single-query kernel: one block of kQ1Threads per SM, so
+// that a block owns (almost) all of the SM's shared memory for its caches.
+constexpr int kQ1Threads = 1024;
+constexpr int kQ1Warps = kQ1Threads / 32;
+
 struct Q1State {
   float *r_u = nullptr, *pi = nullptr, *pic = nullptr;   // residues (sign = marked), reserves, Kahan
   float *t_v = nullptr, *t_a = nullptr;                  // r(v)/d(v), r(a)/W_col(a)
+  float* t_a2 = nullptr;                                 // the other t_A buffer (attribute push)
   uint32_t *list_u = nullptr, *list_v = nullptr, *list_a = nullptr;   // push-round lists
   float* split_acc = nullptr;                            // partial sums of split rows
   uint32_t* split_cnt = nullptr;                         // finished chunks of split rows
@@ -32,6 +38,17 @@ struct Q1Params {
   uint32_t dense_div = 32;     // pull rounds once the frontier covers > 1/dense_div of the edges
   uint32_t n_split = 0;        // split-row slots (phase 1 V + A, phase 2 U)
   uint32_t trace_cap = 0;
+  // Pull rounds and shared memory (dynamic, smem_bytes per block):
+  //   attr_push: the attribute hop of round t+1 is pushed during round t's
+  //     phase 2 into a block-local accumulator over A (shared memory), then
+  //     added to the next t_A; otherwise it is pulled in phase 1 over A->U;
+  //   ta_smem: phase 2 reads t_A from a shared-memory copy.
+  uint32_t smem_bytes = 0;
+  int attr_push = 0;
+  int ta_smem = 0;
+  // short rows of the pull phases: at most vw_max lanes per row (a power of
+  // two, 1..32; 1 = one row per lane)
+  uint32_t vw_max = 32;
   // Theorem 3 mode: start from r = 1 on every U node, run exactly max_rounds
   // synchronous rounds; the reserves are then pi_T and final_maxr_bits[1]
   // holds max_u pi_T(u).
@@ -44,6 +61,10 @@ struct Q1Params {
 
 int launch_query1(const DevGraph& g, const Q1State& s, const Q1Params& p, bool bf16, int grid,
                   cudaStream_t stream);
-int query1_max_grid(bool bf16, int sm_count);
+// Persistent grid of the single-query kernel with smem_bytes of dynamic
+// shared memory per block (-1 if it cannot be made resident).
+int query1_max_grid(bool bf16, int sm_count, uint32_t smem_bytes);
+// Largest dynamic shared memory a block of the single-query kernel may use.
+uint32_t query1_max_smem(int device);
 
 }  // namespace ahpp

@@ -66,6 +66,7 @@ struct ahpp_server {
   uint32_t* d_n = nullptr;
   ahpp_stats* d_stats = nullptr;
   GridBarrier* d_bar = nullptr;
+  BatchParams plan;                      // the batched kernel's shared-memory plan (hub rows)
   SlotState* h_slots = nullptr;          // pinned mirror of the slot table
   std::vector<uint64_t> slot_ticket;
   std::vector<Clock::time_point> slot_submit;
@@ -324,7 +325,7 @@ int ahpp_server_start(ahpp_graph* g, const ahpp_server_opts* opts, ahpp_server**
   if (o.single_max) s->single_max = o.single_max;
   // slots: requested, else what the HBM budget leaves after the graph, else 8 tiles
   const DevGraph& G = g->dg;
-  const size_t n_split = (size_t)G.b_v.n_split + G.b_a.n_split + G.b_u.n_split;
+  const size_t n_split = G.b_split_max;        // any chunk choice fits
   const size_t tile_bytes = (size_t)G.n_u * kTile * 12 + (size_t)std::max(G.n_v, 1u) * kTile * 4 +
                             (size_t)std::max(G.n_a, 1u) * kTile * 4 + std::max<size_t>(n_split, 1) * (kTile + 1) * 4 +
                             (size_t)kRadixPasses * kTile * kRadixBins * 4 + (size_t)kTile * s->kmax * 8 + 4096;
@@ -400,8 +401,11 @@ int ahpp_server_start(ahpp_graph* g, const ahpp_server_opts* opts, ahpp_server**
         cudaMemset(s->d_tile_round, 0, 4ull * tiles) != cudaSuccess ||
         cudaMemset(s->d_slots, 0, sizeof(SlotState) * s->n_slots) != cudaSuccess)
       rc = cuda_fail(cudaGetLastError(), "ahpp_server_start: table upload");
-    s->grid = batch_max_grid(g->bf16, g->sm_count);
-    if (s->grid <= 0) { set_error("ahpp_server_start: occupancy query failed"); rc = AHPP_ECUDA; }
+    if (rc == AHPP_OK) {
+      std::lock_guard<std::mutex> glock(g->mu);
+      rc = batch_plan(g, s->plan);
+      s->grid = g->bt_grid;
+    }
   }
   if (rc != AHPP_OK) {
     s->release();

@@ -136,15 +136,47 @@ def test_concurrent_tile_groups_same_results(ahpp, tiny, groups):
 
 
 def test_autotune_keeps_results(ahpp, tiny):
-    g, lam = tiny["g"], tiny["lam"]
+    """The autotuner picks a shape among its candidates (tile groups, long-row
+    chunk, push/pull cut of the single-query path) and the results under the
+    tuned shape stay within 1e-6 of the oracle push, batched and single."""
+    g, og, lam = tiny["g"], tiny["og"], tiny["lam"]
     G = ahpp.Graph.from_arrays(g, lam=lam, attr_bf16=0)
     try:
         qs = [int(x) for x in synth.draw_queries(g.n_u, 64, seed=75)]
         before, _, _ = G.query_batch_dense(qs, 1e-6)
+        assert G.info["batch_chunk"] == 256 and G.info["single_dense_div"] == 32
         info = G.autotune(qs, 1e-6)
-        assert info["batch_groups"] in (1, 2, 4)
+        assert info["batch_groups"] in (1, 2, 4) and info["batch_tile"] in (16, 32)
+        assert info["batch_chunk"] in (128, 256, 512)
+        assert info["single_dense_div"] in (8, 16, 32, 64, 128)
+        assert info["single_vec_width"] in (1, 2, 8, 32)
+        rep = G.autotune_report()
+        assert "batch_groups=4" in rep and "single_dense_div=128" in rep and all(v > 0 for v in rep.values())
         after, _, rc = G.query_batch_dense(qs, 1e-6)
         assert rc == 0 and np.abs(after - before).max() <= TOL
+        for i in (0, 33, 63):
+            ref = og.push("asrp", ALPHA, BETA, qs[i], 1e-6, lam=lam)
+            assert np.abs(after[i].astype(np.float64) - ref.pi).max() <= TOL
+            one, _, rc1 = G.query_dense(qs[i], 1e-6)
+            assert rc1 == 0 and np.abs(one.astype(np.float64) - ref.pi).max() <= TOL
+    finally:
+        G.close()
+
+
+@pytest.mark.parametrize("chunk", [128, 512])
+def test_every_chunk_choice_matches_oracle(ahpp, tiny, chunk):
+    """Each long-row chunk size the autotuner may pick (set here through the
+    configuration) gives the oracle's result in the batched kernel."""
+    g, og, lam = tiny["g"], tiny["og"], tiny["lam"]
+    G = ahpp.Graph.from_arrays(g, lam=lam, attr_bf16=0, batch_chunk=chunk)
+    try:
+        assert G.info["batch_chunk"] == chunk
+        qs = [int(x) for x in synth.draw_queries(g.n_u, 40, seed=77)]
+        dense, _, rc = G.query_batch_dense(qs, 1e-6)
+        assert rc == 0
+        for i in (0, 17, 39):
+            ref = og.push("asrp", ALPHA, BETA, qs[i], 1e-6, lam=lam)
+            assert np.abs(dense[i].astype(np.float64) - ref.pi).max() <= TOL
     finally:
         G.close()
 

@@ -98,6 +98,23 @@ def test_app_dense_parity(ahpp, tiny, eps):
         G.close()
 
 
+@pytest.mark.parametrize("vw", [1, 2, 4, 8, 16])
+def test_short_row_lane_widths_match_oracle(ahpp, tiny, vw):
+    """The single-query kernel walks short rows with up to vw lanes each (the
+    default 32 is covered by every other test): the same result for each."""
+    G = ahpp.Graph.from_arrays(tiny["g"], lam=tiny["lam"], attr_bf16=0, single_vec_width=vw)
+    try:
+        assert G.info["single_vec_width"] == vw
+        for q in tiny["qs"][:2]:
+            pi, st, rc = G.query_dense(q, 1e-6)
+            assert rc == 0
+            ref = tiny["og"].push("asrp", ALPHA, BETA, q, 1e-6, lam=tiny["lam"])
+            check_dense(pi, ref.pi, tiny["Pi"][q], 1e-6)
+            assert abs(st["rounds"] - ref.stats["rounds"]) <= 1
+    finally:
+        G.close()
+
+
 def topk_overlap(nodes, ref_scores, k, eps):
     """Overlap with the oracle's top-k; nodes whose oracle score lies within
     2 eps of the k-th score are interchangeable (ties of the approximation)."""
@@ -150,6 +167,32 @@ def test_batch_alone_vs_mix(tiny):
         assert stats[i]["rounds"] == st["rounds"]
         ref = tiny["og"].push("asrp", ALPHA, BETA, qs[i], eps[i], lam=tiny["lam"])
         check_dense(dense[i], ref.pi, tiny["Pi"][qs[i]], eps[i])
+
+
+def test_narrow_tiles_match_oracle(ahpp, tiny):
+    """Tiles of 16 queries (the batched kernel's other width): a ragged batch
+    of three tiles with duplicate sources and mixed eps, element by element
+    against the oracle and the same queries in tiles of 32; top-k too."""
+    g, og, lam = tiny["g"], tiny["og"], tiny["lam"]
+    G = ahpp.Graph.from_arrays(g, lam=lam, attr_bf16=0, batch_tile=16)
+    try:
+        assert G.info["batch_tile"] == 16
+        qs = [int(x) for x in synth.draw_queries(g.n_u, 37, seed=8)]
+        qs[3] = qs[4]
+        eps = np.where(np.arange(37) % 3 == 0, 1e-4, 1e-6)
+        dense, stats, rc = G.query_batch_dense(qs, eps)
+        assert rc == 0
+        wide, wstats, _ = tiny["G"].query_batch_dense(qs, eps)
+        assert np.abs(dense - wide).max() <= TOL
+        assert [s["rounds"] for s in stats] == [s["rounds"] for s in wstats]
+        for i in (0, 3, 4, 15, 16, 36):
+            ref = og.push("asrp", ALPHA, BETA, qs[i], float(eps[i]), lam=lam)
+            check_dense(dense[i], ref.pi, tiny["Pi"][qs[i]], float(eps[i]))
+        res = G.query_batch(qs, eps, 30)
+        for i in (0, 16, 36):
+            check_topk(res[i].nodes, res[i].scores, dense[i], 30, float(eps[i]))
+    finally:
+        G.close()
 
 
 def test_batch_topk_matches_single(tiny):

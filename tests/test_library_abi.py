@@ -44,6 +44,7 @@ def test_struct_sizes_match_header(lib):
     c = ahpp.default_config()
     assert c.alpha == 0.15 and c.beta == 0.35 and c.algo == ahpp.AHPP_ASRP
     assert c.attr_bf16 == 1 and c.kahan == 1 and c.lambda_ == 0.0
+    assert c.batch_chunk == 0
 
 
 def test_no_cpu_fallback_without_gpu(lib):
