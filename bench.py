@@ -56,6 +56,9 @@ def parse(argv=None):
                     help="large graph only: scale |U|, |V|, |E| and |A| by this factor (scalability sweep)")
     ap.add_argument("--ablation", type=int, default=3,
                     help="single-query ablation of the ASRP switch rule and APP on N queries (0: off)")
+    ap.add_argument("--scale-leg", type=float, default=0.25,
+                    help="also time batched and plain queries on the large recipe scaled by this factor "
+                         "(the scalability sweep's smallest graph; 0: off)")
     ap.add_argument("--no-autotune", action="store_true",
                     help="keep the default launch shapes (no ahpp_autotune before the timed region)")
     ap.add_argument("--no-exact", action="store_true",
@@ -605,6 +608,10 @@ def run_ours(args, rank, world, local_rank):
     if rank == 0 and args.ablation > 0:
         ablation = run_ablation(ahpp, g, args, info["lambda"], local_rank)
 
+    scale_leg = None
+    if rank == 0 and args.scale_leg > 0 and args.graph == "medium":
+        scale_leg = run_scale_leg(ahpp, args, local_rank)
+
     # roofline of the dominant kernel (the batched persistent launch)
     peak, peak_kind = measured_peak()
     alg = tile_rounds * round_bytes(info, tile) + topk_bytes(info, B)   # one launch (last step)
@@ -666,6 +673,7 @@ def run_ours(args, rank, world, local_rank):
         "served": served,
         "parity": parity,
         "ablation": ablation,
+        "scale_leg": scale_leg,
         "p50_ms": statistics.median(lat_ms),
         "p99_ms": float(np.percentile(lat_ms, 99)),
         "latency_note": "batched: a query completes with its 1,024-query step",
@@ -698,6 +706,8 @@ def run_ours(args, rank, world, local_rank):
         "parity_min_err_vs_exact": _opt(ex.get("min_err_vs_exact"), 3),
         "topk_overlap_vs_exact": ex.get("topk_overlap_vs_exact_min"),
         "bf16_precision_cost_max": _opt(((parity or {}).get("bf16_precision_cost") or {}).get("max_abs"), 3),
+        "large_quarter_batched_qps": _opt(scale_leg and scale_leg["batched_qps"], 4),
+        "large_quarter_vs_plain": _opt(scale_leg and scale_leg["batched_vs_plain"], 3),
     })
     G.close()
     return out
@@ -776,13 +786,15 @@ def parity_vs_oracle(G, cpu, eps, k, exact=None, exact32=None):
 
 def run_ablation(ahpp, g, args, lam, device):
     """Single-query ablation on the same graph (Exp-2's question): ASRP with
-    the switch budget as read (rule 0), as printed (rule 1), never switching
-    (rule 2), and APP; per variant the mean rounds, switch round and the
-    plain-path throughput over args.ablation queries."""
+    the switch budget as read (rule 0) and as printed (rule 1); APP(E), the
+    stricter threshold without the switch (ASRP's rule 2); APP(S), APP's
+    thresholds with the switch; and APP; per variant the mean rounds, switch
+    round and the plain-path throughput over args.ablation queries."""
     import torch
     variants = [("ASRP, switch budget as read (default)", dict(algo=ahpp.AHPP_ASRP, switch_rule=0)),
                 ("ASRP, switch budget as printed", dict(algo=ahpp.AHPP_ASRP, switch_rule=1)),
-                ("ASRP, never switch", dict(algo=ahpp.AHPP_ASRP, switch_rule=2)),
+                ("APP(E): ASRP's eps / lambda threshold, never switch", dict(algo=ahpp.AHPP_ASRP, switch_rule=2)),
+                ("APP(S): APP's thresholds with the synchronous switch", dict(algo=ahpp.AHPP_APP_S)),
                 ("APP", dict(algo=ahpp.AHPP_APP))]
     qs = synth.draw_queries(g.n_u, args.ablation + 1, seed=303)
     dev = torch.device("cuda", device)
@@ -807,6 +819,46 @@ def run_ablation(ahpp, g, args, lam, device):
         finally:
             G.close()
     return out
+
+
+def run_scale_leg(ahpp, args, device):
+    """The large recipe (Zipf(2.0), 30 attributes per node) scaled by
+    args.scale_leg: batched (128 queries, one step after one warm-up step)
+    and plain (two queries after one warm-up) queries/s at the bench's eps,
+    top-1,000 as in the large workload; the smallest graph of the
+    scalability sweep (Exp-3's shape on synthetic graphs)."""
+    import torch
+    spec = synth.scaled(synth.LARGE, args.scale_leg)
+    t0 = time.perf_counter()
+    gl = synth.make_graph(**spec)
+    gen_s = time.perf_counter() - t0
+    G = ahpp.Graph.from_arrays(gl, device=device)
+    try:
+        qs = synth.draw_queries(gl.n_u, 128 * 2 + 3, seed=515)
+        G.query_batch(qs[:128], args.eps, 1000)                 # warm-up step
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        a.record()
+        res = G.query_batch(qs[128:256], args.eps, 1000)
+        b.record()
+        torch.cuda.synchronize()
+        batched = 128 / (a.elapsed_time(b) / 1e3)
+        G.query(int(qs[256]), args.eps, 1000)
+        lat = []
+        for q in qs[257:259]:
+            a.record()
+            G.query(int(q), args.eps, 1000)
+            b.record()
+            torch.cuda.synchronize()
+            lat.append(a.elapsed_time(b))
+        plain = 1e3 / statistics.mean(lat)
+        return {"scale": args.scale_leg, "n_u": gl.n_u, "n_v": gl.n_v, "n_e": gl.n_e, "n_ea": gl.n_ea,
+                "lambda": G.lam, "rounds_mean": float(np.mean([r.stats["rounds"] for r in res])),
+                "batched_qps": batched, "plain_qps": plain, "batched_vs_plain": batched / plain,
+                "generate_s": gen_s,
+                "note": "large recipe scaled (|U|, |V|, |E|, |A|); 128-query batch and 2 plain queries, top-1,000"}
+    finally:
+        G.close()
 
 
 def closed_loop(srv, qs, eps, ks, inflight):

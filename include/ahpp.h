@@ -48,6 +48,11 @@ extern "C" {
 
 #define AHPP_APP 1                /* Algorithm 3 */
 #define AHPP_ASRP 2               /* Algorithm 4 */
+#define AHPP_APP_S 3              /* APP(S) of Exp-2 (Section 5): APP's per-node thresholds
+                                     r_max (|N(u)| + |A(u)|), switching to Algorithm 4's
+                                     synchronous pushes when the push count reaches
+                                     2 (|E| + |E_A|) log_{1/(1-alpha)}(M' / r_max), M' the
+                                     largest r(u) / (|N(u)| + |A(u)|); stops on APP's test */
 
 #define AHPP_MAX_K 4096u          /* largest k accepted by the top-k entry points */
 
@@ -73,12 +78,12 @@ typedef struct {
 typedef struct {
     double alpha;              /* restart probability, (0, 1); default 0.15 */
     double beta;               /* attribute jumping probability, [0, 1]; default 0.35 */
-    int algo;                  /* AHPP_ASRP (default) or AHPP_APP */
+    int algo;                  /* AHPP_ASRP (default), AHPP_APP or AHPP_APP_S */
     double lambda;             /* ASRP's lambda; <= 0: Theorem 3 estimate at load (default) */
     int lambda_T;              /* iterations of the Theorem 3 estimate; 0: ceil(ln(100|U|)/ln(1/(1-alpha))) */
     int attr_bf16;             /* store attribute weights as bfloat16 (default 1) */
     int kahan;                 /* Kahan-compensated FP32 reserves (default 1) */
-    int switch_rule;           /* ASRP switch test: 0 corrected (default), 1 as printed, 2 never */
+    int switch_rule;           /* switch test: 0 corrected (default), 1 as printed (ASRP only), 2 never */
     uint64_t hbm_budget_bytes; /* cap on device memory of graph + query state; 0 = no cap */
     int device;                /* CUDA device ordinal (default 0) */
     uint32_t max_rounds;       /* round cap per query; 0: automatic */

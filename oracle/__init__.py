@@ -36,8 +36,8 @@ import numpy as np
 
 from .build import build_oracle
 
-OG_FP, OG_APP, OG_ASRP = 0, 1, 2
-ALGOS = {"fp": OG_FP, "app": OG_APP, "asrp": OG_ASRP}
+OG_FP, OG_APP, OG_ASRP, OG_APPS = 0, 1, 2, 3
+ALGOS = {"fp": OG_FP, "app": OG_APP, "asrp": OG_ASRP, "apps": OG_APPS}
 
 _u32p = ctypes.POINTER(ctypes.c_uint32)
 _u64p = ctypes.POINTER(ctypes.c_uint64)
@@ -173,7 +173,8 @@ class OracleGraph:
     def push(self, algo: str, alpha: float, beta: float, q: int, eps: float,
              lam: float | None = None, switch_rule: int = 0, max_rounds: int = 1_000_000,
              trace_cap: int = 4096) -> PushResult:
-        """APP (Algorithm 3) or ASRP (Algorithm 4) from q."""
+        """APP (Algorithm 3), ASRP (Algorithm 4) or APP(S) (APP with ASRP's
+        synchronous switch, the ablation arm of Exp-2) from q."""
         pi = np.zeros(self.n_u)
         r_u = np.zeros(self.n_u)
         st = _Stats()

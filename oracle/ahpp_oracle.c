@@ -33,6 +33,13 @@
  *   - A U node without V neighbours (or without attributes) drops the
  *     (1-beta) (or beta) share of its pushed mass; the dropped mass is
  *     reported as "leak".  Eq. 1 and Eq. 2 give such rows no entries.
+ *   - APP(S) of Exp-2 (APP with ASRP's synchronous push operations) is
+ *     APP's per-node thresholds r_max (|N(u)| + |A(u)|) in an asynchronous
+ *     phase, after each of its rounds the switch test above with M / eps_f
+ *     replaced by M' / r_max, M' = max over nodes u with |N(u)| + |A(u)| > 0
+ *     of r(u) / (|N(u)| + |A(u)|) (the largest residue in units of its own
+ *     threshold), then a synchronous phase pushing every positive residue;
+ *     it stops on APP's own test (every residue at or below its threshold).
  */
 #include <math.h>
 #include <stdint.h>
@@ -47,6 +54,7 @@
 #define OG_FP 0
 #define OG_APP 1
 #define OG_ASRP 2
+#define OG_APPS 3     /* APP(S): APP with the synchronous switch */
 
 typedef struct {
     uint64_t n_row, nnz;
@@ -341,7 +349,7 @@ static void og_sums(const og_graph *g, const double *r_u, const double *pi,
 }
 
 /*
- * APP (Algorithm 3) or ASRP (Algorithm 4) from source q.
+ * APP (Algorithm 3), ASRP (Algorithm 4) or APP(S) (Exp-2) from source q.
  *   eps: error threshold; lambda: ASRP's parameter (eps_f = eps / lambda);
  *   switch_rule: 0 = corrected budget (default), 1 = printed formula,
  *                2 = never switch (asynchronous pushes with eps_f only).
@@ -352,9 +360,10 @@ int og_push(const og_graph *g, int algo, double alpha, double beta, uint32_t q,
             double eps, double lambda, int switch_rule, uint32_t max_rounds,
             double *pi, double *r_u_out, og_stats *st, og_trace *tr) {
     if (q >= g->n_u || !(alpha > 0.0 && alpha < 1.0) || !(beta >= 0.0 && beta <= 1.0) ||
-        !(eps > 0.0) || (algo != OG_APP && algo != OG_ASRP) ||
+        !(eps > 0.0) || (algo != OG_APP && algo != OG_ASRP && algo != OG_APPS) ||
         (algo == OG_ASRP && !(lambda > 0.0)))
         return OG_EINVAL;
+    int app_thr = algo == OG_APP || algo == OG_APPS;    /* APP's per-node thresholds */
     uint32_t n = g->n_u;
     double *r_u = calloc(n ? n : 1, sizeof(double));
     double *r_v = calloc(g->n_v ? g->n_v : 1, sizeof(double));
@@ -382,14 +391,16 @@ int og_push(const og_graph *g, int algo, double alpha, double beta, uint32_t q,
         /* loop test of Algorithms 3 and 4: some U residue above its threshold */
         int any = 0;
         for (uint32_t u = 0; u < n && !any; u++) {
-            double th = (algo == OG_APP) ? r_max * (double)cnt[u] : eps_f;
+            double th = app_thr ? r_max * (double)cnt[u] : eps_f;
             if (r_u[u] > th) any = 1;
         }
         if (!any) break;
         if (round >= max_rounds) { rc = OG_ENOTCONVERGED; break; }
         uint64_t nf;
-        if (algo == OG_APP)
+        if (algo == OG_APP || (algo == OG_APPS && !sync))
             nf = og_round(g, alpha, beta, cnt, r_max, r_u, r_v, r_a, pi, sel, &n_p, &leak);
+        else if (algo == OG_APPS)
+            nf = og_round(g, alpha, beta, NULL, 0.0, r_u, r_v, r_a, pi, sel, &n_p, &leak);
         else
             nf = og_round(g, alpha, beta, NULL, sync ? 0.0 : eps_f, r_u, r_v, r_a, pi, sel,
                           &n_p, &leak);
@@ -413,6 +424,13 @@ int og_push(const og_graph *g, int algo, double alpha, double beta, uint32_t q,
                 budget = INFINITY;
             else
                 budget = 2.0 * EE * fmax(0.0, log(m / eps_f) / lg);
+            if ((double)n_p >= budget) { sync = 1; st->switch_round = round + 1; }
+        }
+        if (algo == OG_APPS && !sync) {             /* APP(S): the same test in APP's units */
+            double mrel = 0.0;
+            for (uint32_t u = 0; u < n; u++)
+                if (cnt[u] > 0 && r_u[u] / (double)cnt[u] > mrel) mrel = r_u[u] / (double)cnt[u];
+            double budget = 2.0 * EE * fmax(0.0, log(mrel / r_max) / lg);
             if ((double)n_p >= budget) { sync = 1; st->switch_round = round + 1; }
         }
     }

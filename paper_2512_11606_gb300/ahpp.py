@@ -18,7 +18,7 @@ LIB_PATH = os.environ.get("AHPP_LIB") or os.path.join(HERE, "_build", "libahpp_g
 AHPP_OK, AHPP_EINVAL, AHPP_ENOMEM, AHPP_ECUDA = 0, -1, -2, -3
 AHPP_ENOTCONVERGED, AHPP_EBUSY, AHPP_ETIMEOUT, AHPP_ESTATE = -4, -5, -6, -7
 AHPP_ECANCELED = -8
-AHPP_APP, AHPP_ASRP = 1, 2
+AHPP_APP, AHPP_ASRP, AHPP_APP_S = 1, 2, 3
 AHPP_MAX_K = 4096
 
 _ERRNAMES = {AHPP_EINVAL: "EINVAL", AHPP_ENOMEM: "ENOMEM", AHPP_ECUDA: "ECUDA",

@@ -65,6 +65,14 @@ __global__ void k_batch_wait_status(const WaitBars wb, uint32_t n, ahpp_stats* s
   }
 }
 
+}  // namespace
+
+int kernel_algo(int algo) {
+  return algo == AHPP_APP ? kAlgoAPP : algo == AHPP_ASRP ? kAlgoASRP : algo == AHPP_APP_S ? kAlgoAPPS : -1;
+}
+
+namespace {
+
 int status_code(int status) {
   if (status == kStatusBadArg) { set_error("a query had q outside U or eps <= 0"); return AHPP_EINVAL; }
   if (status == kStatusCap) return AHPP_ENOTCONVERGED;
@@ -79,13 +87,13 @@ uint32_t auto_rounds(double eps_f, double alpha) {
 }
 
 double eps_f_of(const ahpp_graph* g, double eps) {
-  return g->cfg.algo == AHPP_APP ? eps / (double)(g->n_e + g->n_ea) : eps / g->lambda;
+  return g->cfg.algo == AHPP_ASRP ? eps / g->lambda : eps / (double)(g->n_e + g->n_ea);
 }
 
 Q1Params q1_params(const ahpp_graph* g, uint32_t q_new, double eps) {
   Q1Params p;
   p.q = q_new;
-  p.algo = g->cfg.algo == AHPP_APP ? kAlgoAPP : kAlgoASRP;
+  p.algo = kernel_algo(g->cfg.algo);
   p.kahan = g->cfg.kahan;
   p.switch_rule = g->cfg.switch_rule;
   p.eps_f = eps_f_of(g, eps);
@@ -258,7 +266,7 @@ int run_batch_launch(ahpp_graph* g, uint32_t n, const uint32_t* d_q, const doubl
   p.out_dense = d_dense;
   p.u_old2new = g->d_u_old2new;
   p.u_new2old = g->d_u_new2old;
-  p.algo = g->cfg.algo == AHPP_APP ? kAlgoAPP : kAlgoASRP;
+  p.algo = kernel_algo(g->cfg.algo);
   p.kahan = g->cfg.kahan;
   p.switch_rule = g->cfg.switch_rule;
   p.lambda = g->lambda;
@@ -382,8 +390,10 @@ int ahpp_load_graph(const ahpp_graph_desc* desc, const ahpp_config* cfg, ahpp_gr
   ahpp_config c;
   if (cfg) c = *cfg; else ahpp_config_default(&c);
   if (!(c.alpha > 0.0 && c.alpha < 1.0) || !(c.beta >= 0.0 && c.beta <= 1.0) ||
-      (c.algo != AHPP_APP && c.algo != AHPP_ASRP) || c.switch_rule < 0 || c.switch_rule > 2) {
-    set_error("ahpp_load_graph: alpha must be in (0,1), beta in [0,1], algo APP or ASRP");
+      kernel_algo(c.algo) < 0 || c.switch_rule < 0 || c.switch_rule > 2 ||
+      (c.algo == AHPP_APP_S && c.switch_rule == 1)) {
+    set_error("ahpp_load_graph: alpha must be in (0,1), beta in [0,1], algo APP, ASRP or APP_S "
+              "(switch_rule 1, the printed formula, is ASRP's only)");
     return AHPP_EINVAL;
   }
   if (c.batch_tile != 0 && c.batch_tile != 16 && c.batch_tile != 32) {

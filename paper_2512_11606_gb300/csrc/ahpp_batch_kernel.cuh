@@ -167,8 +167,11 @@ struct Q4Partials {
   uint32_t marked[kQL] = {0, 0, 0, 0};
   uint32_t mdeg[kQL] = {0, 0, 0, 0};
   uint32_t np[kQL] = {0, 0, 0, 0};
+  float max_rel[kQL] = {0.f, 0.f, 0.f, 0.f};   // APP(S) statistics (see RAcc)
+  uint32_t above[kQL] = {0, 0, 0, 0};
 };
 
+template <bool APPS>
 __device__ __forceinline__ void flush_q4(Q4Partials& p, RAcc* acc) {
   __shared__ float s_max[kBWarps][32];
   __shared__ uint32_t s_mk[kBWarps][32], s_dg[kBWarps][32], s_np[kBWarps][32];
@@ -181,6 +184,10 @@ __device__ __forceinline__ void flush_q4(Q4Partials& p, RAcc* acc) {
       p.marked[j] += __shfl_xor_sync(kFull, p.marked[j], o);
       p.mdeg[j] += __shfl_xor_sync(kFull, p.mdeg[j], o);
       p.np[j] += __shfl_xor_sync(kFull, p.np[j], o);
+      if (APPS) {
+        p.max_rel[j] = fmaxf(p.max_rel[j], __shfl_xor_sync(kFull, p.max_rel[j], o));
+        p.above[j] += __shfl_xor_sync(kFull, p.above[j], o);
+      }
     }
   }
   if (lane < kGL) {
@@ -205,6 +212,26 @@ __device__ __forceinline__ void flush_q4(Q4Partials& p, RAcc* acc) {
     if (mk) atomicAdd(&a->marked, mk);
     if (dg) atomicAdd(&a->marked_deg, dg);
     if (np) atomicAdd(&a->np_flush, np);
+  }
+  if (APPS) {
+    // the APP(S) statistics through the same buffers (max_r / marked reused)
+    __syncthreads();
+    if (lane < kGL) {
+#pragma unroll
+      for (int j = 0; j < kQL; ++j) {
+        const uint32_t q = lane * kQL + j;
+        s_max[warp][q] = p.max_rel[j];
+        s_mk[warp][q] = p.above[j];
+      }
+    }
+    __syncthreads();
+    if (warp == 0 && lane < kTile) {
+      float m = 0.f;
+      uint32_t ab = 0;
+      for (int w = 0; w < kBWarps; ++w) { m = fmaxf(m, s_max[w][lane]); ab += s_mk[w][lane]; }
+      if (m > 0.f) atomicMax(&acc[lane].max_rel_bits, __float_as_uint(m));
+      if (ab) atomicAdd(&acc[lane].above, ab);
+    }
   }
   __syncthreads();
   p = Q4Partials();
@@ -323,14 +350,14 @@ __device__ __forceinline__ void gphase1(const BCtx& c, RAcc* A, bool do_v, bool 
       part.np[2] += tv.z > 0.f ? d : 0; part.np[3] += tv.w > 0.f ? d : 0;
     }
   }
-  if (count) flush_q4(part, A);
+  if (count) flush_q4<false>(part, A);
 }
 
 // Residue update of row u for this lane's 4 queries: reserve update of the
 // queries that pushed u this round, then the mark for the next round.
 __device__ __forceinline__ float4 gepilogue2(const BCtx& c, uint32_t u, float4 s, uint32_t cnt,
-                                             const float* th, const int* act, const LaneCtl* app_ctl,
-                                             Q4Partials& part) {
+                                             const float* th, const int* act, const int* pn,
+                                             const LaneCtl* ctl, bool apps, Q4Partials& part) {
   float4 pushed = make_float4(0.f, 0.f, 0.f, 0.f);
   if (!(act[0] | act[1] | act[2] | act[3])) return pushed;
   float* pp4 = &pushed.x;
@@ -359,8 +386,12 @@ __device__ __forceinline__ float4 gepilogue2(const BCtx& c, uint32_t u, float4 s
     }
     const float r_new = kept + ss[j];
     part.max_r[j] = fmaxf(part.max_r[j], r_new);
-    const bool mark = app_ctl ? (double)r_new > app_ctl[kQL * gl + j].eps_f * (double)cnt
-                              : r_new >= th[j];
+    const double rmx = ctl[kQL * gl + j].eps_f;           // APP's r_max for per-node thresholds
+    if (apps) {
+      if (cnt) part.max_rel[j] = fmaxf(part.max_rel[j], r_new / (float)cnt);
+      if ((double)r_new > rmx * (double)cnt) part.above[j] += 1;
+    }
+    const bool mark = pn[j] ? (double)r_new > rmx * (double)cnt : r_new >= th[j];
     if (mark) {
       rr[j] = -r_new;
       pp4[j] = r_new;
@@ -412,15 +443,17 @@ __device__ __forceinline__ void gphase2(const BCtx& c, const LaneCtl* ctl, RAcc*
   const DevGraph& g = c.g;
   const uint32_t lane = c.lane, gl = lane & (kGL - 1), gi = lane / kGL;
   const unsigned gmask = ((1u << kGL) - 1u) << (gi * kGL);
-  const bool app = c.p.algo == kAlgoAPP;
-  // mark thresholds and activity of this lane's 4 queries
+  const bool apps = c.p.algo == kAlgoAPPS;
+  // mark thresholds and activity of this lane's 4 queries: APP's per-node
+  // thresholds (pn), or one threshold (eps_f, or 0 once synchronous)
   float th[kQL];
-  int act[kQL];
+  int act[kQL], pn[kQL];
 #pragma unroll
   for (int j = 0; j < kQL; ++j) {
     const LaneCtl& q = ctl[kQL * gl + j];
     act[j] = q.active;
-    th[j] = app ? 0.f : threshold_up(q.phase == kPhaseSync ? 0.0 : q.eps_f);
+    pn[j] = per_node_threshold(c.p.algo, q.phase);
+    th[j] = pn[j] ? 0.f : threshold_up(q.phase == kPhaseSync ? 0.0 : q.eps_f);
   }
   const float* __restrict__ t_v = c.t.t_v;
   const float* __restrict__ t_a = ta_in;
@@ -459,10 +492,11 @@ __device__ __forceinline__ void gphase2(const BCtx& c, const LaneCtl* ctl, RAcc*
       if (!split_combine4(c.t, sl, g.b_u.split_nchunks[slot], s, gl, gmask, &tot)) continue;
       s = tot;
     }
-    const float4 pushed = gepilogue2(c, u, s, dv + da, th, act, app ? ctl : nullptr, part);
+    const float4 pushed = gepilogue2(c, u, s, dv + da, th, act, pn, ctl, apps, part);
     if (ta_push) push_attr<WA>(g, u, pushed, ta_push, gl, gmask);
   }
-  flush_q4(part, A);
+  if (apps) flush_q4<true>(part, A);
+  else flush_q4<false>(part, A);
 }
 
 
@@ -514,7 +548,7 @@ k_tiles(const __grid_constant__ DevGraph g, const __grid_constant__ BatchState s
   const uint32_t lane = c.lane;
   const bool lq = lane < (uint32_t)kTile;               // this lane stands for a query
   const bool warp0 = threadIdx.x < 32;
-  const bool app = p.algo == kAlgoAPP;
+  const bool app = p.algo != kAlgoASRP;   // APP's r_max as eps_f, per-node threshold for the source
   const uint32_t n_work = SERVE ? sv.n_live : (p.n + kTile - 1) / kTile;
   const uint32_t n_split = g.b_v.n_split + g.b_a.n_split + g.b_u.n_split;
   const size_t nu32 = (size_t)g.n_u * kTile;
@@ -646,12 +680,24 @@ k_tiles(const __grid_constant__ DevGraph g, const __grid_constant__ BatchState s
           ++L.rounds;
           const float M = __uint_as_float(__ldcg(&A[lane].max_r_bits));
           L.n_p += s_mdeg[lane] + __ldcg(&A[lane].np_flush);
-          if (!app) {
+          if (p.algo == kAlgoASRP) {
             if ((double)M <= L.eps_f) {
               L.phase = kPhaseDone;
               L.active = 0;
               s_fin[lane] = 1;
             } else if (L.phase == kPhaseAsync && (double)L.n_p >= bbudget(p, L.eps_f, (double)M)) {
+              L.phase = kPhaseSync;
+              L.switch_round = L.rounds + 1;
+              switched = 1;
+            }
+          } else if (p.algo == kAlgoAPPS) {
+            // APP's stopping test; the switch budget in units of APP's thresholds
+            const float Mrel = __uint_as_float(__ldcg(&A[lane].max_rel_bits));
+            if (__ldcg(&A[lane].above) == 0) {
+              L.phase = kPhaseDone;
+              L.active = 0;
+              s_fin[lane] = 1;
+            } else if (L.phase == kPhaseAsync && (double)L.n_p >= bbudget(p, L.eps_f, (double)Mrel)) {
               L.phase = kPhaseSync;
               L.switch_round = L.rounds + 1;
               switched = 1;

@@ -186,7 +186,8 @@ extern "C" int ahpp_load_graph_file(const char* path, const ahpp_config* cfg, ah
     set_error("ahpp_load_graph_file: alpha, beta and attr_bf16 must equal the cached graph's");
     return AHPP_EINVAL;
   }
-  if ((c.algo != AHPP_APP && c.algo != AHPP_ASRP) || c.switch_rule < 0 || c.switch_rule > 2 ||
+  if (kernel_algo(c.algo) < 0 || c.switch_rule < 0 || c.switch_rule > 2 ||
+      (c.algo == AHPP_APP_S && c.switch_rule == 1) ||
       (c.batch_tile != 0 && c.batch_tile != 16 && c.batch_tile != 32) || c.batch_groups > (uint32_t)kMaxGroups ||
       chunk_choice(c.batch_chunk) < 0 || c.single_vec_width > 32 ||
       (c.single_vec_width & (c.single_vec_width - 1))) {

@@ -132,6 +132,8 @@ int reset_barrier(ahpp_graph* g, GridBarrier* bar, cudaStream_t stream, bool kee
 // Synchronous (reads one word from the device on `stream`).
 int barrier_status(GridBarrier* bar, cudaStream_t stream, int* status);
 int build_graph(const ahpp_graph_desc* desc, ahpp_graph* g);
+// The kernels' algorithm id of an AHPP_* constant (-1 if none).
+int kernel_algo(int algo);
 // Shared-memory plan of the single-query kernel (the grid does not depend on
 // it: one block per SM).
 void plan_query1_smem(ahpp_graph* g);

@@ -89,7 +89,15 @@ __device__ __forceinline__ float wload<__nv_bfloat16>(const void* p, uint32_t i)
 
 enum : int { kPhaseAsync = 0, kPhaseSync = 1, kPhaseDone = 2 };
 enum : int { kStatusOk = 0, kStatusCap = 1, kStatusWait = 2, kStatusBadArg = 3 };
-enum : int { kAlgoAPP = 1, kAlgoASRP = 2 };
+// kAlgoAPPS: APP(S), APP's per-node thresholds with ASRP's synchronous switch
+// (the ablation arm of Exp-2).
+enum : int { kAlgoAPP = 1, kAlgoASRP = 2, kAlgoAPPS = 3 };
+
+// Per-node thresholds r_max (|N(u)| + |A(u)|) in this phase (APP, and APP(S)
+// before its switch), else one threshold for every node.
+__device__ __forceinline__ bool per_node_threshold(int algo, int phase) {
+  return algo == kAlgoAPP || (algo == kAlgoAPPS && phase != kPhaseSync);
+}
 
 // Per-query control block (global memory; written by one leader thread,
 // mirrored in registers by every thread of a persistent kernel).
@@ -120,6 +128,10 @@ struct RAcc {
   uint32_t n_list_v, n_list_a;     // push rounds: touched V / A lists
   uint32_t n_list_u;               // push rounds: marked list length
   uint32_t pad;
+  // APP(S): max_u r(u) / (|N(u)| + |A(u)|) after the round (float bits) and
+  // the nodes whose residue exceeds APP's threshold r_max (|N(u)| + |A(u)|)
+  unsigned int max_rel_bits;
+  uint32_t above;
 };
 
 // Software grid barrier for persistent cooperative launches.  Every spin is
@@ -246,6 +258,8 @@ struct Partials {
   unsigned long long marked_deg = 0;
   unsigned long long np_flush = 0;
   double sum_r = 0.0;
+  float max_rel = 0.f;       // APP(S) statistics (see RAcc)
+  uint32_t above = 0;
 };
 
 // Block reduction of Partials into acc (one atomic per field per block);
@@ -256,18 +270,28 @@ __device__ __forceinline__ void flush_partials(Partials& p, RAcc* acc) {
   __shared__ uint32_t s_marked[NW];
   __shared__ unsigned long long s_deg[NW], s_np[NW];
   __shared__ double s_sum[NW];
+  __shared__ float s_rel[NW];
+  __shared__ uint32_t s_above[NW];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   float m = warp_max(p.max_r);
   uint32_t mk = warp_sum_u32(p.marked);
   unsigned long long dg = warp_sum_u64(p.marked_deg);
   unsigned long long np = warp_sum_u64(p.np_flush);
   double sm = warp_sum_d(p.sum_r);
-  if (lane == 0) { s_max[warp] = m; s_marked[warp] = mk; s_deg[warp] = dg; s_np[warp] = np; s_sum[warp] = sm; }
+  float rel = warp_max(p.max_rel);
+  uint32_t ab = warp_sum_u32(p.above);
+  if (lane == 0) {
+    s_max[warp] = m; s_marked[warp] = mk; s_deg[warp] = dg; s_np[warp] = np; s_sum[warp] = sm;
+    s_rel[warp] = rel; s_above[warp] = ab;
+  }
   __syncthreads();
   if (threadIdx.x == 0) {
     for (int w = 1; w < NW; ++w) {
       m = fmaxf(m, s_max[w]); mk += s_marked[w]; dg += s_deg[w]; np += s_np[w]; sm += s_sum[w];
+      rel = fmaxf(rel, s_rel[w]); ab += s_above[w];
     }
+    if (rel > 0.f) atomicMax(&acc->max_rel_bits, __float_as_uint(rel));
+    if (ab) atomicAdd(&acc->above, ab);
     if (m > 0.f) atomicMax(&acc->max_r_bits, __float_as_uint(m));
     if (mk) atomicAdd(&acc->marked, mk);
     if (dg) atomicAdd(&acc->marked_deg, dg);

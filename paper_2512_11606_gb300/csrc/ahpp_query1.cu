@@ -60,21 +60,51 @@ __device__ __forceinline__ void p1_epilogue(const Ctx& c, bool is_a, uint32_t ro
   }
 }
 
-// sum_k coef[k] * x(idx[k]) over a warp's share of a long row: lane l takes entries
-// z + l, z + l + 32, ... (two per step).
+// sum over k = k0, k0 + st, k0 + 2 st, ... < e of coef(k) x(idx[k]), in that
+// order, four entries per step, software-pipelined: the next step's indices
+// and coefficients load while this step's gathers are in flight, so a step
+// waits for one load latency instead of two (index, then gather).
+template <typename CoefF, typename XF>
+__device__ __forceinline__ float strided_dot(uint32_t k0, uint32_t e, uint32_t st, const uint32_t* __restrict__ idx,
+                                             CoefF coef, XF x, float s) {
+  uint32_t i0 = 0, i1 = 0, i2 = 0, i3 = 0;
+  float c0 = 0.f, c1 = 0.f, c2 = 0.f, c3 = 0.f;
+  auto load = [&](uint32_t k, uint32_t& j0, uint32_t& j1, uint32_t& j2, uint32_t& j3, float& d0, float& d1,
+                  float& d2, float& d3) {
+    if (k < e) { j0 = idx[k]; d0 = coef(k); }
+    if (k + st < e) { j1 = idx[k + st]; d1 = coef(k + st); }
+    if (k + 2 * st < e) { j2 = idx[k + 2 * st]; d2 = coef(k + 2 * st); }
+    if (k + 3 * st < e) { j3 = idx[k + 3 * st]; d3 = coef(k + 3 * st); }
+  };
+  load(k0, i0, i1, i2, i3, c0, c1, c2, c3);
+  for (uint32_t k = k0; k < e; k += 4 * st) {
+    uint32_t n0 = 0, n1 = 0, n2 = 0, n3 = 0;
+    float d0 = 0.f, d1 = 0.f, d2 = 0.f, d3 = 0.f;
+    load(k + 4 * st, n0, n1, n2, n3, d0, d1, d2, d3);
+    const float x0 = x(i0);
+    const float x1 = k + st < e ? x(i1) : 0.f;
+    const float x2 = k + 2 * st < e ? x(i2) : 0.f;
+    const float x3 = k + 3 * st < e ? x(i3) : 0.f;
+    s = fmaf(c0, x0, s);
+    if (k + st < e) s = fmaf(c1, x1, s);
+    if (k + 2 * st < e) s = fmaf(c2, x2, s);
+    if (k + 3 * st < e) s = fmaf(c3, x3, s);
+    i0 = n0; i1 = n1; i2 = n2; i3 = n3;
+    c0 = d0; c1 = d1; c2 = d2; c3 = d3;
+  }
+  return s;
+}
+
+// The first index >= e of the sequence k0, k0 + st, ... (k0 itself if >= e).
+__device__ __forceinline__ uint32_t strided_end(uint32_t k0, uint32_t e, uint32_t st) {
+  return k0 < e ? k0 + (e - k0 + st - 1) / st * st : k0;
+}
+
+// A warp's share of a long row: lane l takes entries z + l, z + l + 32, ...
 template <typename CoefF, typename XF>
 __device__ __forceinline__ float lane_dot(uint32_t z, uint32_t w, uint32_t lane, const uint32_t* __restrict__ idx,
                                           CoefF coef, XF x, float s) {
-  uint32_t k = z + lane;
-  for (; k + 32 < w; k += 64) {
-    const uint32_t i0 = idx[k], i1 = idx[k + 32];
-    const float c0 = coef(k), c1 = coef(k + 32);
-    const float x0 = x(i0), x1 = x(i1);
-    s = fmaf(c0, x0, s);
-    s = fmaf(c1, x1, s);
-  }
-  if (k < w) s = fmaf(coef(k), x(idx[k]), s);
-  return s;
+  return strided_dot(z + lane, w, 32u, idx, coef, x, s);
 }
 
 // Lanes per row for an item of nr short rows holding nnz entries: the mean
@@ -90,25 +120,6 @@ __device__ __forceinline__ uint32_t vec_width(uint32_t nnz, uint32_t nr, uint32_
 // Sum over the vw lanes of a row's segment (every lane of the warp calls it).
 __device__ __forceinline__ float seg_sum(float s, uint32_t vw) {
   for (uint32_t o = vw >> 1; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-  return s;
-}
-
-// sum over k = b, b + vw, b + 2 vw, ... < e of coef(k) x(idx[k]), four
-// entries per step (their loads are in flight together); returns the sum and
-// leaves k at the first index >= e of the sequence.
-template <typename CoefF, typename XF>
-__device__ __forceinline__ float strided_dot(uint32_t& k, uint32_t e, uint32_t vw, const uint32_t* __restrict__ idx,
-                                             CoefF coef, XF x, float s) {
-  for (; k + 3 * vw < e; k += 4 * vw) {
-    const uint32_t i0 = idx[k], i1 = idx[k + vw], i2 = idx[k + 2 * vw], i3 = idx[k + 3 * vw];
-    const float c0 = coef(k), c1 = coef(k + vw), c2 = coef(k + 2 * vw), c3 = coef(k + 3 * vw);
-    const float x0 = x(i0), x1 = x(i1), x2 = x(i2), x3 = x(i3);
-    s = fmaf(c0, x0, s);
-    s = fmaf(c1, x1, s);
-    s = fmaf(c2, x2, s);
-    s = fmaf(c3, x3, s);
-  }
-  for (; k < e; k += vw) s = fmaf(coef(k), x(idx[k]), s);
   return s;
 }
 
@@ -180,8 +191,7 @@ __device__ void phase1(const Ctx& c, Partials& part, bool do_a, float* ta_out, c
       const uint32_t r0 = item.x, nr = item.y;
       const uint32_t vw = vec_width(off[r0 + nr] - off[r0], nr, c.p.vw_max);
       const float mine = rows_to_lanes(nr, vw, lane, [&](uint32_t r, uint32_t sub) {
-        uint32_t k = off[r0 + r] + sub;
-        const uint32_t e = off[r0 + r + 1];
+        const uint32_t k = off[r0 + r] + sub, e = off[r0 + r + 1];
         return is_a ? strided_dot(k, e, vw, idx, ca, P, 0.f) : strided_dot(k, e, vw, idx, cv, P, 0.f);
       });
       if (lane < nr) p1_epilogue(c, is_a, r0 + lane, mine, ta_out, part);
@@ -195,6 +205,13 @@ __device__ void phase1(const Ctx& c, Partials& part, bool do_a, float* ta_out, c
 // with the attribute push, the marked node's attribute share of the next
 // round: acc[a] += w(u,a) rnorm_u[u] p_u (block-local, shared memory), added
 // to t_A' scaled by k_attr cnorm_a[a] at the end of the phase.
+
+// APP(S)'s round statistics of a residue r of a node with cnt = |N(u)| + |A(u)|:
+// the largest r / cnt, and whether r exceeds APP's threshold r_max cnt.
+__device__ __forceinline__ void app_stats(const Ctx& c, float r, uint32_t cnt, Partials& part) {
+  if (cnt) part.max_rel = fmaxf(part.max_rel, r / (float)cnt);
+  if ((double)r > c.p.eps_f * (double)cnt) part.above += 1;
+}
 
 // Returns the residue marked for the next push (0 if u is not marked).
 __device__ __forceinline__ float p2_epilogue(const Ctx& c, uint32_t u, float s, uint32_t cnt,
@@ -215,6 +232,7 @@ __device__ __forceinline__ float p2_epilogue(const Ctx& c, uint32_t u, float s, 
   const float r_new = kept + s;
   part.max_r = fmaxf(part.max_r, r_new);
   part.sum_r += (double)r_new;
+  if (c.p.algo == kAlgoAPPS) app_stats(c, r_new, cnt, part);
   const double th = per_node ? theta * (double)cnt : theta;
   if ((double)r_new > th) {
     c.s.r_u[u] = -r_new;
@@ -296,10 +314,10 @@ __device__ void phase2(const Ctx& c, double theta, bool per_node, Partials& part
         const uint32_t u = u0 + r;
         const uint32_t b1 = g.uv_off[u], dv = g.uv_off[u + 1] - b1;
         const uint32_t b2 = g.ua_off[u], da = g.ua_off[u + 1] - b2;
-        uint32_t k = b1 + sub;
-        float s = strided_dot(k, b1 + dv, vw, g.uv_idx, wv, TV, 0.f);
-        k = k - b1 - dv + b2;              // the same lane's first attribute entry
-        return strided_dot(k, b2 + da, vw, g.ua_idx, wa, TA, s);
+        const float s = strided_dot(b1 + sub, b1 + dv, vw, g.uv_idx, wv, TV, 0.f);
+        // the same lane's first attribute entry
+        const uint32_t ka = strided_end(b1 + sub, b1 + dv, vw) - b1 - dv + b2;
+        return strided_dot(ka, b2 + da, vw, g.ua_idx, wa, TA, s);
       });
       if (lane < nr) {
         const uint32_t u = u0 + lane;
@@ -390,8 +408,13 @@ __device__ void flush_va(const Ctx& c, uint32_t nv, uint32_t na, Partials& part)
     for (uint32_t k = b + lane; k < e; k += 32) {
       const float w = is_a ? wload<WA>(g.au_w, k) : g.vu_w[k];
       const float add = w * val;
-      const float old = atomicAdd(&c.s.r_u[idx[k]], add);
+      const uint32_t j = idx[k];
+      const float old = atomicAdd(&c.s.r_u[j], add);
       part.max_r = fmaxf(part.max_r, old + add);
+      // APP(S): a node's last update sees its new residue (counts of nodes
+      // above threshold may repeat a node; only zero is tested)
+      if (c.p.algo == kAlgoAPPS)
+        app_stats(c, old + add, (g.uv_off[j + 1] - g.uv_off[j]) + (g.ua_off[j + 1] - g.ua_off[j]), part);
     }
   }
 }
@@ -451,7 +474,7 @@ __device__ __forceinline__ double budget_of(const Q1Params& p, double M) {
 }  // namespace
 
 template <typename WA>
-__global__ void __launch_bounds__(kQ1Threads, 1)
+__global__ void __launch_bounds__(kQ1Threads, kQ1Blocks)
 k_query1(const __grid_constant__ DevGraph g, const __grid_constant__ Q1State s,
          const __grid_constant__ Q1Params p) {
   extern __shared__ __align__(16) float q1_smem[];
@@ -459,7 +482,7 @@ k_query1(const __grid_constant__ DevGraph g, const __grid_constant__ Q1State s,
         blockIdx.x * kQ1Threads + threadIdx.x, gridDim.x * kQ1Threads};
   const bool leader = blockIdx.x == 0 && threadIdx.x == 0;
   const unsigned int nb = gridDim.x;
-  const bool app = p.algo == kAlgoAPP;
+  const bool app = p.algo != kAlgoASRP;    // APP's per-node threshold for the source
 
   // ---- init: zero the state, mark the source (the initial state of Algorithm 3)
   const float r0 = p.lambda_mode ? -1.f : 0.f;
@@ -522,7 +545,8 @@ k_query1(const __grid_constant__ DevGraph g, const __grid_constant__ Q1State s,
     if (!dense && marked_deg * (unsigned long long)p.dense_div > (unsigned long long)p.e_tot) dense = 1;
     if (p.trace_cap && leader && rounds < p.trace_cap) s.trace_frontier[rounds] = marked;
     pushes += marked;
-    const double theta = app ? p.eps_f : (phase == kPhaseSync ? 0.0 : p.eps_f);
+    const bool per_node = per_node_threshold(p.algo, phase);
+    const double theta = (phase == kPhaseSync && !per_node) ? 0.0 : p.eps_f;
 
     if (!dense) {
       push_u<WA>(c, marked, A);
@@ -538,7 +562,7 @@ k_query1(const __grid_constant__ DevGraph g, const __grid_constant__ Q1State s,
       phase1<WA>(c, part, do_a, ta_cur, do_a ? nullptr : ta_cur, ta_next);
       flush_partials<kQ1Warps>(part, A);
       if (!grid_sync(s.bar, nb)) { status = kStatusWait; break; }
-      phase2<WA>(c, theta, app, part, ta_cur, ta_next, q1_smem);
+      phase2<WA>(c, theta, per_node, part, ta_cur, ta_next, q1_smem);
       flush_partials<kQ1Warps>(part, A);
       if (!grid_sync(s.bar, nb)) { status = kStatusWait; break; }
       if (p.attr_push) ta_sel ^= 1;
@@ -552,7 +576,7 @@ k_query1(const __grid_constant__ DevGraph g, const __grid_constant__ Q1State s,
     n_p += marked_deg + __ldcg(&A->np_flush);
     if (p.trace_cap && leader && rounds - 1 < p.trace_cap) s.trace_maxr[rounds - 1] = M;
     bool switched = false;
-    if (!app) {
+    if (p.algo == kAlgoASRP) {
       if ((double)M <= p.eps_f) {
         phase = kPhaseDone;
       } else if (phase == kPhaseAsync && (double)n_p >= budget_of(p, (double)M)) {
@@ -560,11 +584,22 @@ k_query1(const __grid_constant__ DevGraph g, const __grid_constant__ Q1State s,
         switch_round = rounds + 1;
         switched = true;
       }
+    } else if (p.algo == kAlgoAPPS) {
+      // APP's stopping test; the switch budget in units of APP's thresholds
+      const float Mrel = __uint_as_float(__ldcg(&A->max_rel_bits));
+      if (__ldcg(&A->above) == 0) {
+        phase = kPhaseDone;
+      } else if (phase == kPhaseAsync && (double)n_p >= budget_of(p, (double)Mrel)) {
+        phase = kPhaseSync;
+        switch_round = rounds + 1;
+        switched = true;
+      }
     }
     if (phase == kPhaseDone) break;
     if (!dense) {
-      const double th_next = app ? p.eps_f : (phase == kPhaseSync ? 0.0 : p.eps_f);
-      select_frontier(c, th_next, app, A, part);
+      const bool pn_next = per_node_threshold(p.algo, phase);
+      const double th_next = (phase == kPhaseSync && !pn_next) ? 0.0 : p.eps_f;
+      select_frontier(c, th_next, pn_next, A, part);
       flush_partials<kQ1Warps>(part, A);
       if (!grid_sync(s.bar, nb)) { status = kStatusWait; break; }
     } else if (switched) {
@@ -619,15 +654,19 @@ const void* q1_fn(bool bf16) {
 }
 }  // namespace
 
-void prefer_l1(bool bf16) {
-  static bool done[2] = {false, false};
-  if (!done[bf16]) {
-    // only the planned shared memory is carved out; the rest stays L1, which
-    // holds the lines of the rows the lanes are walking
-    cudaFuncSetAttribute(q1_fn(bf16), cudaFuncAttributePreferredSharedMemoryCarveout,
-                         (int)cudaSharedmemCarveoutMaxL1);
-    done[bf16] = true;
-  }
+// Carve out of the SM's unified memory just the shared memory kQ1Blocks
+// blocks need (each with 1 KB reserved by the system); the rest stays L1,
+// which holds the lines of the rows the lanes are walking.
+int carve_out(bool bf16, uint32_t smem_bytes) {
+  int dev = 0, per_sm = 0;
+  cudaFuncAttributes fa{};
+  if (cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&per_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev) != cudaSuccess ||
+      cudaFuncGetAttributes(&fa, q1_fn(bf16)) != cudaSuccess || per_sm <= 0)
+    return (int)cudaGetLastError();
+  const uint64_t need = (uint64_t)kQ1Blocks * (smem_bytes + fa.sharedSizeBytes + 1024);
+  const int pct = (int)std::min<uint64_t>(100, (100 * need + per_sm - 1) / per_sm);
+  return (int)cudaFuncSetAttribute(q1_fn(bf16), cudaFuncAttributePreferredSharedMemoryCarveout, pct);
 }
 
 uint32_t query1_max_smem(int device) {
@@ -648,9 +687,9 @@ uint32_t query1_max_smem(int device) {
 int launch_query1(const DevGraph& g, const Q1State& s, const Q1Params& p, bool bf16,
                   int grid, cudaStream_t stream) {
   void* args[] = {(void*)&g, (void*)&s, (void*)&p};
-  prefer_l1(bf16);
   cudaError_t e = cudaFuncSetAttribute(q1_fn(bf16), cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)p.smem_bytes);
+  if (e == cudaSuccess) e = (cudaError_t)carve_out(bf16, p.smem_bytes);
   if (e == cudaSuccess)
     e = cudaLaunchCooperativeKernel(q1_fn(bf16), dim3(grid), dim3(kQ1Threads), args, p.smem_bytes, stream);
   return e == cudaSuccess ? 0 : (int)e;
@@ -658,9 +697,9 @@ int launch_query1(const DevGraph& g, const Q1State& s, const Q1Params& p, bool b
 
 int query1_max_grid(bool bf16, int sm_count, uint32_t smem_bytes) {
   int per_sm = 0;
-  prefer_l1(bf16);
   cudaError_t e = cudaFuncSetAttribute(q1_fn(bf16), cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)smem_bytes);
+  if (e == cudaSuccess) e = (cudaError_t)carve_out(bf16, smem_bytes);
   if (e == cudaSuccess)
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, q1_fn(bf16), kQ1Threads, smem_bytes);
   if (e != cudaSuccess || per_sm <= 0) {

@@ -189,7 +189,7 @@ int server_step(ahpp_server* s) {
       s->queue.pop_front();
       SlotState& S = s->h_slots[slot];
       std::memset(&S, 0, sizeof(S));
-      S.eps_f = g->cfg.algo == AHPP_APP ? r.eps / (double)(g->n_e + g->n_ea) : r.eps / g->lambda;
+      S.eps_f = g->cfg.algo == AHPP_ASRP ? r.eps / g->lambda : r.eps / (double)(g->n_e + g->n_ea);
       S.q_new = g->h_u_old2new[r.q];
       S.k = (uint32_t)std::min<uint64_t>(r.k, g->n_u);
       S.state = kSlotNew;
@@ -217,7 +217,7 @@ int server_step(ahpp_server* s) {
   p.out_stats = s->d_stats;
   p.u_old2new = g->d_u_old2new;
   p.u_new2old = g->d_u_new2old;
-  p.algo = g->cfg.algo == AHPP_APP ? kAlgoAPP : kAlgoASRP;
+  p.algo = kernel_algo(g->cfg.algo);
   p.kahan = g->cfg.kahan;
   p.switch_rule = g->cfg.switch_rule;
   p.lambda = g->lambda;

@@ -199,6 +199,37 @@ def test_batched_app_matches_oracle(ahpp, tiny):
         G.close()
 
 
+def test_batched_and_served_apps_match_oracle(ahpp, tiny):
+    """APP(S) in the batched kernel (per-lane thresholds, switch and stopping
+    test) and through the server: each query within 1e-6 of the oracle push
+    and of the same query alone."""
+    g, og = tiny["g"], tiny["og"]
+    G = ahpp.Graph.from_arrays(g, algo=ahpp.AHPP_APP_S, attr_bf16=0)
+    try:
+        qs = [int(x) for x in synth.draw_queries(g.n_u, 35, seed=78)]
+        eps = np.where(np.arange(35) % 2 == 0, 1e-6, 1e-4)
+        dense, stats, rc = G.query_batch_dense(qs, eps)
+        assert rc == 0
+        for i in [0, 1, 17, 33, 34]:
+            ref = og.push("apps", ALPHA, BETA, qs[i], float(eps[i]))
+            assert np.abs(dense[i].astype(np.float64) - ref.pi).max() <= TOL
+            assert abs(stats[i]["rounds"] - ref.stats["rounds"]) <= 1
+            assert abs(stats[i]["switch_round"] - ref.stats["switch_round"]) <= 1
+            one, st1, _ = G.query_dense(qs[i], float(eps[i]))
+            assert np.abs(one - dense[i]).max() <= TOL
+        srv = ahpp.Server(G, max_slots=32, rounds_per_step=3, single_max=-1)
+        try:
+            t = [srv.submit(qs[i], float(eps[i]), 40) for i in range(35)]
+            res = [srv.wait(x, 40) for x in t]
+        finally:
+            srv.stop()
+        for i in [0, 17, 34]:
+            assert res[i].rc == 0
+            check_topk(res[i].nodes, res[i].scores, dense[i], 40, float(eps[i]))
+    finally:
+        G.close()
+
+
 def test_empty_batch_and_k_clamped(ahpp, tiny):
     G, g = tiny["G"], tiny["g"]
     assert G.query_batch([], 1e-6, 10) == []

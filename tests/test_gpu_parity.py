@@ -115,6 +115,25 @@ def test_short_row_lane_widths_match_oracle(ahpp, tiny, vw):
         G.close()
 
 
+@pytest.mark.parametrize("eps", [1e-4, 1e-6])
+def test_apps_dense_parity(ahpp, tiny, eps):
+    """APP(S) (APP's thresholds with the synchronous switch, Exp-2's ablation
+    arm): the single-query kernel follows the oracle's trajectory (rounds,
+    switch round) and every reserve is within 1e-6 of the oracle push."""
+    G = ahpp.Graph.from_arrays(tiny["g"], algo=ahpp.AHPP_APP_S, attr_bf16=0)
+    try:
+        for q in tiny["qs"][:3]:
+            pi_gpu, st, rc = G.query_dense(q, eps)
+            assert rc == 0 and st["status"] == 0
+            ref = tiny["og"].push("apps", ALPHA, BETA, q, eps)
+            check_dense(pi_gpu, ref.pi, tiny["Pi"][q], eps)
+            assert abs(st["rounds"] - ref.stats["rounds"]) <= 1
+            assert abs(st["switch_round"] - ref.stats["switch_round"]) <= 1
+            assert ref.stats["switch_round"] > 0 or eps > 1e-5
+    finally:
+        G.close()
+
+
 def topk_overlap(nodes, ref_scores, k, eps):
     """Overlap with the oracle's top-k; nodes whose oracle score lies within
     2 eps of the k-th score are interchangeable (ties of the approximation)."""

@@ -191,6 +191,24 @@ def test_app_trajectory_closed_form_on_hub_graph(n, eps):
     check_hub_run(res, n, q, R, 0)
 
 
+@pytest.mark.parametrize("n,eps", [(5, 1e-6), (17, 1e-9), (2, 3e-4)])
+def test_apps_trajectory_closed_form_on_hub_graph(n, eps):
+    """APP(S) (APP with ASRP's synchronous switch, the ablation arm of Exp-2)
+    on P = J/n: every node has |N(u)| + |A(u)| = 2, so APP's threshold is
+    r_max * 2 = eps / n for all of them and the largest residue in units of
+    its threshold is M / 2 / r_max = M n / eps.  The run is therefore ASRP's
+    hand trajectory with eps_f = eps / n (lambda = n) under the read budget:
+    the same switch round, rounds, n_p, traces and reserves."""
+    R, sr, cuts = hub_trajectory(n, eps, float(n), 0)
+    for c in cuts:
+        assert abs(c - round(c)) > 1e-6 or abs(c) > 1e6
+    og = oracle.OracleGraph.from_arrays(hub_graph(n))
+    q = n // 3
+    res = og.push("apps", ALPHA, BETA, q, eps)
+    check_hub_run(res, n, q, R, sr)
+    assert sr > 0 or R <= 2
+
+
 def check_hub_run(res, n, q, R, sr):
     s, t = res.stats, res.trace
     assert res.rc == 0
@@ -400,7 +418,7 @@ def test_theorem2_error_bound(tiny, eps):
     """Theorem 2: 0 <= pi - pi_hat <= eps with the certified lambda; APP too."""
     og, Pi, q, lam = tiny["og"], tiny["Pi"], tiny["q"], tiny["lam"]
     exact = Pi[q]
-    for algo in ("asrp", "app"):
+    for algo in ("asrp", "app", "apps"):
         res = og.push(algo, ALPHA, BETA, q, eps, lam=lam)
         assert res.rc == 0
         err = exact - res.pi
@@ -471,6 +489,37 @@ def test_asrp_selection_rule_of_each_phase(tiny):
             wider = True
             break
     assert wider
+
+
+def test_apps_phases_and_stopping_rule(tiny):
+    """APP(S): asynchronous rounds push exactly the nodes above APP's
+    per-node threshold r_max (|N(u)| + |A(u)|), synchronous rounds every
+    positive residue; the switch fires on the budget in APP's units; the run
+    stops on APP's test (no residue above its threshold) and ends earlier
+    than APP alone on the tiny graph."""
+    og, q = tiny["og"], tiny["q"]
+    eps = 1e-6
+    EE = og.n_e + og.n_ea
+    r_max = eps / EE
+    g = tiny["g"]              # distinct pairs only (synth merges duplicates), so counts are tuples
+    cnt = (np.bincount(g.e_u, minlength=g.n_u) + np.bincount(g.ea_u, minlength=g.n_u)).astype(np.float64)
+    full = og.push("apps", ALPHA, BETA, q, eps)
+    s, t = full.stats, full.trace
+    sr, R = s["switch_round"], s["rounds"]
+    assert 2 < sr < R
+    for j in sorted({2, 3, sr - 1, sr, sr + 1, R}):
+        before = og.push("apps", ALPHA, BETA, q, eps, max_rounds=j - 1)
+        sync = j >= sr
+        want = int((before.r_u > 0).sum()) if sync else int((before.r_u > r_max * cnt).sum())
+        assert t["frontier"][j - 1] == want, (j, sync)
+    # the budget test that fired, with M' = max r(u) / (|N(u)| + |A(u)|)
+    before = og.push("apps", ALPHA, BETA, q, eps, max_rounds=sr - 1)
+    mrel = (before.r_u[cnt > 0] / cnt[cnt > 0]).max()
+    budget = 2 * EE * max(0.0, math.log(mrel / r_max) / math.log(1 / (1 - ALPHA)))
+    assert t["n_p"][sr - 2] >= budget
+    assert np.all(full.r_u <= r_max * cnt)
+    app = og.push("app", ALPHA, BETA, q, eps)
+    assert R < app.stats["rounds"]
 
 
 def test_asrp_topk_precision_against_exact(tiny):
