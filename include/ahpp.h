@@ -93,7 +93,7 @@ typedef struct {
     uint32_t batch_chunk;      /* entries per chunk of a long row in the batched kernel: 128, 256 or
                                   512; 0: 256 (ahpp_autotune picks one) */
     uint32_t single_vec_width; /* single-query kernel: at most this many lanes walk one short row
-                                  (1, 2, 4, 8, 16 or 32); 0: 32 (ahpp_autotune picks one) */
+                                  (1, 2, 4, 8, 16 or 32); 0: 2 (ahpp_autotune picks one) */
 } ahpp_config;
 
 /* Per-query statistics. */

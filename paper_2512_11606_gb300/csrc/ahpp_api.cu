@@ -425,7 +425,7 @@ int ahpp_load_graph(const ahpp_graph_desc* desc, const ahpp_config* cfg, ahpp_gr
   g->device = c.device;
   g->batch_tile = c.batch_tile ? c.batch_tile : (uint32_t)ahpp::kTile;
   g->batch_groups = c.batch_groups ? c.batch_groups : 1;
-  g->q1_vw_max = c.single_vec_width ? c.single_vec_width : 32;
+  g->q1_vw_max = c.single_vec_width ? c.single_vec_width : ahpp::kQ1VecWidthDefault;
   int rc = AHPP_OK;
   if (cudaDeviceGetAttribute(&g->sm_count, cudaDevAttrMultiProcessorCount, c.device) != cudaSuccess ||
       cudaStreamCreateWithFlags(&g->stream, cudaStreamNonBlocking) != cudaSuccess) {

@@ -208,7 +208,7 @@ extern "C" int ahpp_load_graph_file(const char* path, const ahpp_config* cfg, ah
   g->device = c.device;
   g->batch_tile = c.batch_tile ? c.batch_tile : (uint32_t)kTile;
   g->batch_groups = c.batch_groups ? c.batch_groups : 1;
-  g->q1_vw_max = c.single_vec_width ? c.single_vec_width : 32;
+  g->q1_vw_max = c.single_vec_width ? c.single_vec_width : ahpp::kQ1VecWidthDefault;
   g->n_u = h.n_u; g->n_v = h.n_v; g->n_a = h.n_a; g->n_e = h.n_e; g->n_ea = h.n_ea;
   g->bf16 = h.attr_bf16 != 0;
   int rc = AHPP_OK;

@@ -98,7 +98,7 @@ struct ahpp_graph {
   uint32_t q1_smem = 0;
   int q1_attr_push = 0, q1_ta_smem = 0;
   uint32_t q1_dense_div = 32;     // pull rounds once the frontier covers > 1/dense_div of the edges
-  uint32_t q1_vw_max = 32;        // lanes per short row in the pull phases (at most)
+  uint32_t q1_vw_max = ahpp::kQ1VecWidthDefault;   // lanes per short row in the pull phases (at most)
   std::string tune_log;           // the last autotune's measurements (JSON object)
   uint32_t n_split1 = 0;
   uint64_t q1_bytes = 0;

@@ -98,10 +98,10 @@ def test_app_dense_parity(ahpp, tiny, eps):
         G.close()
 
 
-@pytest.mark.parametrize("vw", [1, 2, 4, 8, 16])
+@pytest.mark.parametrize("vw", [1, 4, 8, 16, 32])
 def test_short_row_lane_widths_match_oracle(ahpp, tiny, vw):
     """The single-query kernel walks short rows with up to vw lanes each (the
-    default 32 is covered by every other test): the same result for each."""
+    default 2 is covered by every other test): the same result for each."""
     G = ahpp.Graph.from_arrays(tiny["g"], lam=tiny["lam"], attr_bf16=0, single_vec_width=vw)
     try:
         assert G.info["single_vec_width"] == vw
