@@ -341,20 +341,25 @@ def topk_bytes(info, queries):
     return queries * 4 * info["n_u"]
 
 
-# DRAM bytes (read + write) per tile-round of k_tiles on the medium graph, from
-# the ncu capture summarised in profiles/k_tiles_medium_tile32.md (257.40 GB over
-# the 106 rounds of one 32-query tile).  It describes the kernel built from the
-# sources listed by hash; once any of them changes the figure no longer applies.
+# DRAM and L2 -> SM bytes of the two push kernels on the medium graph, from
+# ncu captures summarised under profiles/ (k_tiles: one 32-query tile, per
+# tile-round; k_query1: one query, per pull round).  Each figure describes
+# the kernel built from the sources listed by code digest; once the code of
+# any of them changes (comments and layout aside) the figure no longer
+# applies and ncu_traffic returns None.
 NCU_TRAFFIC = {
-    "graph": "medium",
-    "bytes_per_tile_round": 257.40e9 / 106,
-    # l1tex__m_xbar2l1tex_read_bytes.sum of the same capture: bytes moved from L2 to the SMs
-    "l2_to_sm_bytes_per_tile_round": 944.894883e9 / 106,
-    # code_digest of the kernel sources at capture (raw sha256 prefixes then:
-    # ahpp_batch.cu de4b77bce76bf143, ahpp_batch.cuh f3dfbbd4287bd668,
-    # ahpp_internal.cuh b85a585f011dc3c6)
-    "sources": {"ahpp_batch.cu": "f93e83d641d310da", "ahpp_batch.cuh": "88a9e3865a4bf806",
-                "ahpp_internal.cuh": "aa651509cd78fba7"},
+    "k_tiles": {
+        "graph": "medium",
+        "bytes_per_unit": None,              # dram__bytes_read.sum + dram__bytes_write.sum per tile-round
+        "l2_to_sm_bytes_per_unit": None,     # l1tex__m_xbar2l1tex_read_bytes.sum per tile-round
+        "sources": {},
+    },
+    "k_query1": {
+        "graph": "medium",
+        "bytes_per_unit": None,              # per pull round
+        "l2_to_sm_bytes_per_unit": None,
+        "sources": {},
+    },
 }
 
 
@@ -386,18 +391,20 @@ def code_digest(text):
     return hashlib.sha256(code.encode()).hexdigest()[:16]
 
 
-def ncu_traffic(graph, tile_rounds, key="bytes_per_tile_round"):
-    """Bytes of one launch scaled from the capture (DRAM by default, or the
-    L2 -> SM bytes), or None if it does not describe the kernel as built now
-    (the code of a source file, comments aside, differs from the captured)."""
-    if graph != NCU_TRAFFIC["graph"]:
+def ncu_traffic(kernel, graph, units, key="bytes_per_unit"):
+    """Bytes of one launch scaled from the capture of `kernel` (DRAM by
+    default, or the L2 -> SM bytes) by its units (tile-rounds or pull
+    rounds), or None if no capture describes the kernel as built now (the
+    code of a source file, comments aside, differs from the captured)."""
+    rec = NCU_TRAFFIC[kernel]
+    if graph != rec["graph"] or rec[key] is None or not rec["sources"]:
         return None
     csrc = os.path.join(ROOT, "paper_2512_11606_gb300", "csrc")
-    for name, want in NCU_TRAFFIC["sources"].items():
+    for name, want in rec["sources"].items():
         with open(os.path.join(csrc, name), encoding="utf-8") as f:
             if code_digest(f.read()) != want:
                 return None
-    return NCU_TRAFFIC[key] * tile_rounds
+    return rec[key] * units
 
 
 def row_roofline(ahpp, info, tile_rounds, launch_s, device):
@@ -583,6 +590,9 @@ def run_ours(args, rank, world, local_rank):
         plain["roofline"] = {"bound": "hbm", "kernel": "k_query1", "achieved": ach_p, "peak": peak_p,
                              "unit": "GB/s", "frac": ach_p / peak_p,
                              "algorithmic_bytes_per_pull_round": q1_round_bytes(info),
+                             "traffic": ncu_traffic("k_query1", args.graph, statistics.mean(p_dense)),
+                             "traffic_note": ("ncu DRAM bytes per pull round of one query "
+                                              "(profiles/k_query1_medium.md) x the mean pull rounds"),
                              "peak_source": f"{peak_kind_p} hbm_gbs (MEASURED_PEAKS.json)"}
 
     # serving: open-loop Poisson arrivals on the same graph (continuous batching)
@@ -617,9 +627,10 @@ def run_ours(args, rank, world, local_rank):
     alg = tile_rounds * round_bytes(info, tile) + topk_bytes(info, B)   # one launch (last step)
     achieved = alg / (sum(launch_ms) / K / 1e3) / 1e9
     roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-            "frac": achieved / peak, "traffic": ncu_traffic(args.graph, tile_rounds),
+            "frac": achieved / peak, "traffic": ncu_traffic("k_tiles", args.graph, tile_rounds),
             "traffic_note": ("ncu dram__bytes_read.sum + dram__bytes_write.sum of one 32-query tile "
-                             "(106 rounds), scaled by the launch's tile-rounds"),
+                             "per tile-round (profiles/k_tiles_medium_tile32.md), scaled by the launch's "
+                             "tile-rounds"),
             "peak_source": f"{peak_kind} hbm_gbs (MEASURED_PEAKS.json)",
             "kernel": "k_tiles (persistent: all rounds + top-k of one 1,024-query step)",
             "algorithmic_bytes_per_launch": alg,
@@ -631,7 +642,7 @@ def run_ours(args, rank, world, local_rank):
         roof["l2_rows"] = {"error": str(e)}
     # L2 -> SM bytes (ncu capture, scaled) against the measured rate of random
     # 128-byte row gathers from an L2-resident table of the t_V size
-    l2_bytes = ncu_traffic(args.graph, tile_rounds, "l2_to_sm_bytes_per_tile_round")
+    l2_bytes = ncu_traffic("k_tiles", args.graph, tile_rounds, "l2_to_sm_bytes_per_unit")
     parts = roof["l2_rows"].get("parts") if isinstance(roof.get("l2_rows"), dict) else None
     if l2_bytes and parts:
         peak_l2 = parts[1]["peak_rows_per_s"] * 4 * int(info["batch_tile"]) / 1e9

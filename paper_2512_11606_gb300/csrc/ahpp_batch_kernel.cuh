@@ -355,9 +355,12 @@ __device__ __forceinline__ void gphase1(const BCtx& c, RAcc* A, bool do_v, bool 
 
 // Residue update of row u for this lane's 4 queries: reserve update of the
 // queries that pushed u this round, then the mark for the next round.
+// APPLIKE: APP or APP(S) (per-node thresholds possible, r_max read per query);
+// APPS: APP(S)'s round statistics too.  ASRP launches compile neither.
+template <bool APPLIKE, bool APPS>
 __device__ __forceinline__ float4 gepilogue2(const BCtx& c, uint32_t u, float4 s, uint32_t cnt,
                                              const float* th, const int* act, const int* pn,
-                                             const LaneCtl* ctl, bool apps, Q4Partials& part) {
+                                             const LaneCtl* ctl, Q4Partials& part) {
   float4 pushed = make_float4(0.f, 0.f, 0.f, 0.f);
   if (!(act[0] | act[1] | act[2] | act[3])) return pushed;
   float* pp4 = &pushed.x;
@@ -386,12 +389,17 @@ __device__ __forceinline__ float4 gepilogue2(const BCtx& c, uint32_t u, float4 s
     }
     const float r_new = kept + ss[j];
     part.max_r[j] = fmaxf(part.max_r[j], r_new);
-    const double rmx = ctl[kQL * gl + j].eps_f;           // APP's r_max for per-node thresholds
-    if (apps) {
-      if (cnt) part.max_rel[j] = fmaxf(part.max_rel[j], r_new / (float)cnt);
-      if ((double)r_new > rmx * (double)cnt) part.above[j] += 1;
+    bool mark;
+    if (APPLIKE) {
+      const double rmx = ctl[kQL * gl + j].eps_f;         // APP's r_max for per-node thresholds
+      if (APPS) {
+        if (cnt) part.max_rel[j] = fmaxf(part.max_rel[j], r_new / (float)cnt);
+        if ((double)r_new > rmx * (double)cnt) part.above[j] += 1;
+      }
+      mark = pn[j] ? (double)r_new > rmx * (double)cnt : r_new >= th[j];
+    } else {
+      mark = r_new >= th[j];
     }
-    const bool mark = pn[j] ? (double)r_new > rmx * (double)cnt : r_new >= th[j];
     if (mark) {
       rr[j] = -r_new;
       pp4[j] = r_new;
@@ -437,13 +445,12 @@ __device__ __forceinline__ void push_attr(const DevGraph& g, uint32_t u, float4 
 }
 
 // Phase 2: new residues of every U node for the tile's 32 queries.
-template <typename WA>
+template <typename WA, bool APPLIKE, bool APPS>
 __device__ __forceinline__ void gphase2(const BCtx& c, const LaneCtl* ctl, RAcc* A,
                                         const float* ta_in, float* ta_push) {
   const DevGraph& g = c.g;
   const uint32_t lane = c.lane, gl = lane & (kGL - 1), gi = lane / kGL;
   const unsigned gmask = ((1u << kGL) - 1u) << (gi * kGL);
-  const bool apps = c.p.algo == kAlgoAPPS;
   // mark thresholds and activity of this lane's 4 queries: APP's per-node
   // thresholds (pn), or one threshold (eps_f, or 0 once synchronous)
   float th[kQL];
@@ -452,7 +459,7 @@ __device__ __forceinline__ void gphase2(const BCtx& c, const LaneCtl* ctl, RAcc*
   for (int j = 0; j < kQL; ++j) {
     const LaneCtl& q = ctl[kQL * gl + j];
     act[j] = q.active;
-    pn[j] = per_node_threshold(c.p.algo, q.phase);
+    pn[j] = APPLIKE ? per_node_threshold(c.p.algo, q.phase) : 0;
     th[j] = pn[j] ? 0.f : threshold_up(q.phase == kPhaseSync ? 0.0 : q.eps_f);
   }
   const float* __restrict__ t_v = c.t.t_v;
@@ -492,11 +499,10 @@ __device__ __forceinline__ void gphase2(const BCtx& c, const LaneCtl* ctl, RAcc*
       if (!split_combine4(c.t, sl, g.b_u.split_nchunks[slot], s, gl, gmask, &tot)) continue;
       s = tot;
     }
-    const float4 pushed = gepilogue2(c, u, s, dv + da, th, act, pn, ctl, apps, part);
+    const float4 pushed = gepilogue2<APPLIKE, APPS>(c, u, s, dv + da, th, act, pn, ctl, part);
     if (ta_push) push_attr<WA>(g, u, pushed, ta_push, gl, gmask);
   }
-  if (apps) flush_q4<true>(part, A);
-  else flush_q4<false>(part, A);
+  flush_q4<APPS>(part, A);
 }
 
 
@@ -668,7 +674,9 @@ k_tiles(const __grid_constant__ DevGraph g, const __grid_constant__ BatchState s
       float* ta_next = (tround & 1) ? tb.t_a : tb.t_a2;    // t_A of the next round
       gphase1<WA>(c, A, true, false, nullptr, ta_cur, ta_next, true);
       if (!grid_sync(tb.bar, nbg)) { wait_fail = true; break; }
-      gphase2<WA>(c, s_ctl, A, ta_cur, ta_next);
+      if (p.algo == kAlgoASRP) gphase2<WA, false, false>(c, s_ctl, A, ta_cur, ta_next);
+      else if (p.algo == kAlgoAPP) gphase2<WA, true, false>(c, s_ctl, A, ta_cur, ta_next);
+      else gphase2<WA, true, true>(c, s_ctl, A, ta_cur, ta_next);
       if (!grid_sync(tb.bar, nbg)) { wait_fail = true; break; }
       ++tround;
 

@@ -263,8 +263,8 @@ struct Partials {
 };
 
 // Block reduction of Partials into acc (one atomic per field per block);
-// NW = warps per block.
-template <int NW>
+// NW = warps per block; APPS: also APP(S)'s max_rel and above.
+template <int NW, bool APPS = false>
 __device__ __forceinline__ void flush_partials(Partials& p, RAcc* acc) {
   __shared__ float s_max[NW];
   __shared__ uint32_t s_marked[NW];
@@ -278,8 +278,8 @@ __device__ __forceinline__ void flush_partials(Partials& p, RAcc* acc) {
   unsigned long long dg = warp_sum_u64(p.marked_deg);
   unsigned long long np = warp_sum_u64(p.np_flush);
   double sm = warp_sum_d(p.sum_r);
-  float rel = warp_max(p.max_rel);
-  uint32_t ab = warp_sum_u32(p.above);
+  float rel = APPS ? warp_max(p.max_rel) : 0.f;
+  uint32_t ab = APPS ? warp_sum_u32(p.above) : 0u;
   if (lane == 0) {
     s_max[warp] = m; s_marked[warp] = mk; s_deg[warp] = dg; s_np[warp] = np; s_sum[warp] = sm;
     s_rel[warp] = rel; s_above[warp] = ab;
@@ -288,10 +288,10 @@ __device__ __forceinline__ void flush_partials(Partials& p, RAcc* acc) {
   if (threadIdx.x == 0) {
     for (int w = 1; w < NW; ++w) {
       m = fmaxf(m, s_max[w]); mk += s_marked[w]; dg += s_deg[w]; np += s_np[w]; sm += s_sum[w];
-      rel = fmaxf(rel, s_rel[w]); ab += s_above[w];
+      if (APPS) { rel = fmaxf(rel, s_rel[w]); ab += s_above[w]; }
     }
-    if (rel > 0.f) atomicMax(&acc->max_rel_bits, __float_as_uint(rel));
-    if (ab) atomicAdd(&acc->above, ab);
+    if (APPS && rel > 0.f) atomicMax(&acc->max_rel_bits, __float_as_uint(rel));
+    if (APPS && ab) atomicAdd(&acc->above, ab);
     if (m > 0.f) atomicMax(&acc->max_r_bits, __float_as_uint(m));
     if (mk) atomicAdd(&acc->marked, mk);
     if (dg) atomicAdd(&acc->marked_deg, dg);

@@ -214,6 +214,7 @@ __device__ __forceinline__ void app_stats(const Ctx& c, float r, uint32_t cnt, P
 }
 
 // Returns the residue marked for the next push (0 if u is not marked).
+template <bool APPS>
 __device__ __forceinline__ float p2_epilogue(const Ctx& c, uint32_t u, float s, uint32_t cnt,
                                              double theta, bool per_node, Partials& part) {
   float r_old = c.s.r_u[u];
@@ -232,7 +233,7 @@ __device__ __forceinline__ float p2_epilogue(const Ctx& c, uint32_t u, float s, 
   const float r_new = kept + s;
   part.max_r = fmaxf(part.max_r, r_new);
   part.sum_r += (double)r_new;
-  if (c.p.algo == kAlgoAPPS) app_stats(c, r_new, cnt, part);
+  if (APPS) app_stats(c, r_new, cnt, part);
   const double th = per_node ? theta * (double)cnt : theta;
   if ((double)r_new > th) {
     c.s.r_u[u] = -r_new;
@@ -251,7 +252,7 @@ __device__ __forceinline__ void push_attr_smem(const DevGraph& g, uint32_t u, fl
   for (uint32_t k = b; k < e; ++k) atomicAdd(&acc[g.ua_idx[k]], wload<WA>(g.ua_w, k) * f);
 }
 
-template <typename WA>
+template <typename WA, bool APPS>
 __device__ void phase2(const Ctx& c, double theta, bool per_node, Partials& part, const float* ta_cur,
                        float* ta_next, float* smem) {
   const DevGraph& g = c.g;
@@ -295,10 +296,10 @@ __device__ void phase2(const Ctx& c, double theta, bool per_node, Partials& part
           if (atomicAdd(&c.s.split_cnt[slot], 1u) == nch - 1) {
             float tot = atomicExch(&c.s.split_acc[slot], 0.f);
             c.s.split_cnt[slot] = 0;
-            pm = p2_epilogue(c, u, tot, dv + da, theta, per_node, part);
+            pm = p2_epilogue<APPS>(c, u, tot, dv + da, theta, per_node, part);
           }
         } else {
-          pm = p2_epilogue(c, u, s, dv + da, theta, per_node, part);
+          pm = p2_epilogue<APPS>(c, u, s, dv + da, theta, per_node, part);
         }
         if (ta_next && pm > 0.f) push_attr_smem<WA>(g, u, pm, s_acc);
       }
@@ -322,7 +323,7 @@ __device__ void phase2(const Ctx& c, double theta, bool per_node, Partials& part
       if (lane < nr) {
         const uint32_t u = u0 + lane;
         const uint32_t cnt = (g.uv_off[u + 1] - g.uv_off[u]) + (g.ua_off[u + 1] - g.ua_off[u]);
-        const float pm = p2_epilogue(c, u, mine, cnt, theta, per_node, part);
+        const float pm = p2_epilogue<APPS>(c, u, mine, cnt, theta, per_node, part);
         if (ta_next && pm > 0.f) push_attr_smem<WA>(g, u, pm, s_acc);
       }
     }
@@ -387,7 +388,7 @@ __device__ void push_u(const Ctx& c, uint32_t n_list, RAcc* acc) {
   }
 }
 
-template <typename WA>
+template <typename WA, bool APPS>
 __device__ void flush_va(const Ctx& c, uint32_t nv, uint32_t na, Partials& part) {
   const DevGraph& g = c.g;
   const uint32_t lane = lane_id();
@@ -413,7 +414,7 @@ __device__ void flush_va(const Ctx& c, uint32_t nv, uint32_t na, Partials& part)
       part.max_r = fmaxf(part.max_r, old + add);
       // APP(S): a node's last update sees its new residue (counts of nodes
       // above threshold may repeat a node; only zero is tested)
-      if (c.p.algo == kAlgoAPPS)
+      if (APPS)
         app_stats(c, old + add, (g.uv_off[j + 1] - g.uv_off[j]) + (g.ua_off[j + 1] - g.ua_off[j]), part);
     }
   }
@@ -473,7 +474,7 @@ __device__ __forceinline__ double budget_of(const Q1Params& p, double M) {
 
 }  // namespace
 
-template <typename WA>
+template <typename WA, bool APPS>
 __global__ void __launch_bounds__(kQ1Threads, kQ1Blocks)
 k_query1(const __grid_constant__ DevGraph g, const __grid_constant__ Q1State s,
          const __grid_constant__ Q1Params p) {
@@ -552,18 +553,18 @@ k_query1(const __grid_constant__ DevGraph g, const __grid_constant__ Q1State s,
       push_u<WA>(c, marked, A);
       if (!grid_sync(s.bar, nb)) { status = kStatusWait; break; }
       const uint32_t nv = __ldcg(&A->n_list_v), na = __ldcg(&A->n_list_a);
-      flush_va<WA>(c, nv, na, part);
-      flush_partials<kQ1Warps>(part, A);
+      flush_va<WA, APPS>(c, nv, na, part);
+      flush_partials<kQ1Warps, APPS>(part, A);
       if (!grid_sync(s.bar, nb)) { status = kStatusWait; break; }
     } else {
       float* ta_cur = ta_buf[ta_sel];
       float* ta_next = p.attr_push ? ta_buf[ta_sel ^ 1] : nullptr;
       const bool do_a = !p.attr_push || pull_a;
       phase1<WA>(c, part, do_a, ta_cur, do_a ? nullptr : ta_cur, ta_next);
-      flush_partials<kQ1Warps>(part, A);
+      flush_partials<kQ1Warps, APPS>(part, A);
       if (!grid_sync(s.bar, nb)) { status = kStatusWait; break; }
-      phase2<WA>(c, theta, per_node, part, ta_cur, ta_next, q1_smem);
-      flush_partials<kQ1Warps>(part, A);
+      phase2<WA, APPS>(c, theta, per_node, part, ta_cur, ta_next, q1_smem);
+      flush_partials<kQ1Warps, APPS>(part, A);
       if (!grid_sync(s.bar, nb)) { status = kStatusWait; break; }
       if (p.attr_push) ta_sel ^= 1;
       pull_a = false;
@@ -584,7 +585,7 @@ k_query1(const __grid_constant__ DevGraph g, const __grid_constant__ Q1State s,
         switch_round = rounds + 1;
         switched = true;
       }
-    } else if (p.algo == kAlgoAPPS) {
+    } else if (APPS) {
       // APP's stopping test; the switch budget in units of APP's thresholds
       const float Mrel = __uint_as_float(__ldcg(&A->max_rel_bits));
       if (__ldcg(&A->above) == 0) {
@@ -600,11 +601,11 @@ k_query1(const __grid_constant__ DevGraph g, const __grid_constant__ Q1State s,
       const bool pn_next = per_node_threshold(p.algo, phase);
       const double th_next = (phase == kPhaseSync && !pn_next) ? 0.0 : p.eps_f;
       select_frontier(c, th_next, pn_next, A, part);
-      flush_partials<kQ1Warps>(part, A);
+      flush_partials<kQ1Warps, APPS>(part, A);
       if (!grid_sync(s.bar, nb)) { status = kStatusWait; break; }
     } else if (switched) {
       mark_remaining(c, part);
-      flush_partials<kQ1Warps>(part, A);
+      flush_partials<kQ1Warps, APPS>(part, A);
       if (!grid_sync(s.bar, nb)) { status = kStatusWait; break; }
       pull_a = true;       // the new marks did not push their attribute share
     }
@@ -640,33 +641,42 @@ k_query1(const __grid_constant__ DevGraph g, const __grid_constant__ Q1State s,
   }
 }
 
-template __global__ void k_query1<float>(const __grid_constant__ DevGraph,
-                                         const __grid_constant__ Q1State,
-                                         const __grid_constant__ Q1Params);
-template __global__ void k_query1<__nv_bfloat16>(const __grid_constant__ DevGraph,
-                                                 const __grid_constant__ Q1State,
-                                                 const __grid_constant__ Q1Params);
+#define AHPP_Q1_INSTANCE(WA, APPS)                                                   \
+  template __global__ void k_query1<WA, APPS>(const __grid_constant__ DevGraph,      \
+                                              const __grid_constant__ Q1State,       \
+                                              const __grid_constant__ Q1Params);
+AHPP_Q1_INSTANCE(float, false)
+AHPP_Q1_INSTANCE(__nv_bfloat16, false)
+AHPP_Q1_INSTANCE(float, true)
+AHPP_Q1_INSTANCE(__nv_bfloat16, true)
+#undef AHPP_Q1_INSTANCE
 
 // Launch helper: persistent cooperative grid (one block per SM).
 namespace {
-const void* q1_fn(bool bf16) {
-  return bf16 ? (const void*)k_query1<__nv_bfloat16> : (const void*)k_query1<float>;
+// The instance of a launch: APP(S)'s round statistics are compiled only into
+// the APP(S) instances.
+const void* q1_fn(bool bf16, bool apps = false) {
+  if (apps) return bf16 ? (const void*)k_query1<__nv_bfloat16, true> : (const void*)k_query1<float, true>;
+  return bf16 ? (const void*)k_query1<__nv_bfloat16, false> : (const void*)k_query1<float, false>;
 }
 }  // namespace
 
 // Carve out of the SM's unified memory just the shared memory kQ1Blocks
 // blocks need (each with 1 KB reserved by the system); the rest stays L1,
-// which holds the lines of the rows the lanes are walking.
-int carve_out(bool bf16, uint32_t smem_bytes) {
+// which holds the lines of the rows the lanes are walking.  Sets the dynamic
+// shared memory limit of the instance too.
+int prepare(const void* fn, uint32_t smem_bytes) {
   int dev = 0, per_sm = 0;
   cudaFuncAttributes fa{};
   if (cudaGetDevice(&dev) != cudaSuccess ||
       cudaDeviceGetAttribute(&per_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev) != cudaSuccess ||
-      cudaFuncGetAttributes(&fa, q1_fn(bf16)) != cudaSuccess || per_sm <= 0)
+      cudaFuncGetAttributes(&fa, fn) != cudaSuccess || per_sm <= 0)
     return (int)cudaGetLastError();
+  cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_bytes);
+  if (e != cudaSuccess) return (int)e;
   const uint64_t need = (uint64_t)kQ1Blocks * (smem_bytes + fa.sharedSizeBytes + 1024);
   const int pct = (int)std::min<uint64_t>(100, (100 * need + per_sm - 1) / per_sm);
-  return (int)cudaFuncSetAttribute(q1_fn(bf16), cudaFuncAttributePreferredSharedMemoryCarveout, pct);
+  return (int)cudaFuncSetAttribute(fn, cudaFuncAttributePreferredSharedMemoryCarveout, pct);
 }
 
 uint32_t query1_max_smem(int device) {
@@ -675,38 +685,44 @@ uint32_t query1_max_smem(int device) {
     cudaGetLastError();
     return 0;
   }
-  cudaFuncAttributes fa{};
-  if (cudaFuncGetAttributes(&fa, q1_fn(true)) != cudaSuccess) {
-    cudaGetLastError();
-    return 0;
+  size_t stat = 0;
+  for (int apps = 0; apps < 2; ++apps) {
+    cudaFuncAttributes fa{};
+    if (cudaFuncGetAttributes(&fa, q1_fn(true, apps)) != cudaSuccess) {
+      cudaGetLastError();
+      return 0;
+    }
+    stat = std::max(stat, fa.sharedSizeBytes);
   }
-  const long room = (long)optin - (long)fa.sharedSizeBytes - 1024;   // static shared memory + margin
+  const long room = (long)optin - (long)stat - 1024;   // static shared memory + margin
   return room > 0 ? (uint32_t)(room / 16 * 16) : 0u;
 }
 
 int launch_query1(const DevGraph& g, const Q1State& s, const Q1Params& p, bool bf16,
                   int grid, cudaStream_t stream) {
   void* args[] = {(void*)&g, (void*)&s, (void*)&p};
-  cudaError_t e = cudaFuncSetAttribute(q1_fn(bf16), cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)p.smem_bytes);
-  if (e == cudaSuccess) e = (cudaError_t)carve_out(bf16, p.smem_bytes);
+  const void* fn = q1_fn(bf16, p.algo == kAlgoAPPS);
+  cudaError_t e = (cudaError_t)prepare(fn, p.smem_bytes);
   if (e == cudaSuccess)
-    e = cudaLaunchCooperativeKernel(q1_fn(bf16), dim3(grid), dim3(kQ1Threads), args, p.smem_bytes, stream);
+    e = cudaLaunchCooperativeKernel(fn, dim3(grid), dim3(kQ1Threads), args, p.smem_bytes, stream);
   return e == cudaSuccess ? 0 : (int)e;
 }
 
+// Co-resident grid of both instances (a plan serves every algorithm).
 int query1_max_grid(bool bf16, int sm_count, uint32_t smem_bytes) {
-  int per_sm = 0;
-  cudaError_t e = cudaFuncSetAttribute(q1_fn(bf16), cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)smem_bytes);
-  if (e == cudaSuccess) e = (cudaError_t)carve_out(bf16, smem_bytes);
-  if (e == cudaSuccess)
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, q1_fn(bf16), kQ1Threads, smem_bytes);
-  if (e != cudaSuccess || per_sm <= 0) {
-    cudaGetLastError();
-    return -1;
+  int best = -1;
+  for (int apps = 0; apps < 2; ++apps) {
+    const void* fn = q1_fn(bf16, apps);
+    int per_sm = 0;
+    cudaError_t e = (cudaError_t)prepare(fn, smem_bytes);
+    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, kQ1Threads, smem_bytes);
+    if (e != cudaSuccess || per_sm <= 0) {
+      cudaGetLastError();
+      return -1;
+    }
+    best = best < 0 ? per_sm : std::min(best, per_sm);
   }
-  return per_sm * sm_count;
+  return best * sm_count;
 }
 
 }  // namespace ahpp

@@ -47,12 +47,23 @@ def test_row_roofline_composes_the_measured_rates():
 
 
 def test_ncu_traffic_applies_only_to_the_captured_sources(monkeypatch):
-    assert bench.ncu_traffic("tiny", 10) is None
-    good = dict(bench.NCU_TRAFFIC)
-    bad = dict(good, sources=dict(good["sources"], **{"ahpp_batch.cu": "0000000000000000"}))
-    monkeypatch.setattr(bench, "NCU_TRAFFIC", bad)
-    assert bench.ncu_traffic("medium", 10) is None
-    assert bench.ncu_traffic("medium", 10, "l2_to_sm_bytes_per_tile_round") is None
+    """A capture's bytes scale by the launch's units while every listed
+    source has the captured code digest; another graph, a changed source or
+    a missing capture give None."""
+    csrc = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))),
+                        "paper_2512_11606_gb300", "csrc")
+    digest = bench.code_digest(open(os.path.join(csrc, "ahpp_batch.cuh"), encoding="utf-8").read())
+    rec = {"graph": "medium", "bytes_per_unit": 2.0, "l2_to_sm_bytes_per_unit": 3.0,
+           "sources": {"ahpp_batch.cuh": digest}}
+    monkeypatch.setattr(bench, "NCU_TRAFFIC", {"k_tiles": rec, "k_query1": dict(rec, bytes_per_unit=None)})
+    assert bench.ncu_traffic("k_tiles", "medium", 10) == 20.0
+    assert bench.ncu_traffic("k_tiles", "medium", 10, "l2_to_sm_bytes_per_unit") == 30.0
+    assert bench.ncu_traffic("k_tiles", "tiny", 10) is None
+    assert bench.ncu_traffic("k_query1", "medium", 10) is None
+    bad = dict(rec, sources={"ahpp_batch.cuh": "0000000000000000"})
+    monkeypatch.setattr(bench, "NCU_TRAFFIC", {"k_tiles": bad, "k_query1": bad})
+    assert bench.ncu_traffic("k_tiles", "medium", 10) is None
+    assert bench.ncu_traffic("k_tiles", "medium", 10, "l2_to_sm_bytes_per_unit") is None
 
 
 class FakeServer:
