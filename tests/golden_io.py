@@ -13,7 +13,7 @@ class Fixture:
 
 def load(name):
     f = Fixture()
-    f.edges, f.attrs, f.ps_rows, f.pa_rows = [], [], {}, {}
+    f.edges, f.attrs, f.ps_rows, f.pa_rows, f.kv = [], [], {}, {}, {}
     with open(os.path.join(GOLDEN, name)) as fh:
         for line in fh:
             line = line.split("#", 1)[0].strip()
@@ -29,6 +29,8 @@ def load(name):
             elif tok[0] in ("ps_row", "pa_row"):
                 row = [Fraction(t) for t in tok[2:]]
                 getattr(f, tok[0] + "s")[int(tok[1])] = row
+            else:                       # any other key: its values as fractions
+                f.kv[tok[0]] = [Fraction(t) for t in tok[1:]]
     e = np.array(f.edges) if f.edges else np.zeros((0, 3))
     a = np.array(f.attrs) if f.attrs else np.zeros((0, 3))
     f.e_u, f.e_v, f.e_w = e[:, 0].astype(np.uint32), e[:, 1].astype(np.uint32), e[:, 2]

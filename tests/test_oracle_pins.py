@@ -544,3 +544,16 @@ def test_topk_matches_sorting(tiny):
     nodes, vals = oracle.topk(s, 50)
     order = np.lexsort((np.arange(500), -s))[:50]
     assert np.array_equal(nodes, order) and np.array_equal(vals, s[order])
+
+
+def test_forward_push_fifo_hand_trace():
+    """Algorithm 2's FIFO order, traced by hand (tests/golden/forward_push_fifo.txt):
+    the reserves, residues and push count after the queue empties.  A stack
+    order, or a node re-queued before its neighbours, ends elsewhere."""
+    fx = load("forward_push_fifo.txt")
+    og = oracle.OracleGraph(fx.n_u, fx.n_v, fx.n_a, fx.e_u, fx.e_v, fx.e_w, fx.ea_u, fx.ea_a, fx.ea_w)
+    alpha, beta, eps, q = (float(x) for x in fx.kv["fp_params"])
+    res = og.forward_push(alpha, beta, int(q), eps)
+    assert res.rc == 0 and res.stats["pushes"] == int(fx.kv["fp_pushes"][0])
+    assert list(res.pi) == [float(x) for x in fx.kv["fp_pi"]]          # dyadic: exact in FP64
+    assert list(res.r_u) == [float(x) for x in fx.kv["fp_r"]]
