@@ -12,6 +12,7 @@
 #include <algorithm>
 
 #include "ahpp_host.h"
+#include "../../include/ahpp_measure.h"
 
 namespace ahpp {
 namespace {

@@ -1,4 +1,6 @@
-"""The C-ABI library builds, loads, and exports every entry point of include/ahpp.h.
+"""The C-ABI library builds, loads, and exports every entry point that
+include/*.h declares (the query API in ahpp.h, the measurement helpers in
+ahpp_measure.h).
 
 No kernel runs here: on a machine without a GPU the library must refuse
 (AHPP_ECUDA), never fall back to the CPU.
@@ -22,9 +24,13 @@ def lib():
 
 
 def header_functions():
-    src = open(os.path.join(ROOT, "include", "ahpp.h")).read()
-    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
-    return sorted(set(re.findall(r"\b(ahpp_[a-z_]+)\s*\(", src)))
+    inc = os.path.join(ROOT, "include")
+    names = set()
+    for h in sorted(os.listdir(inc)):
+        if h.endswith(".h"):
+            src = re.sub(r"/\*.*?\*/", "", open(os.path.join(inc, h)).read(), flags=re.S)
+            names |= set(re.findall(r"\b(ahpp_[a-z_]+)\s*\(", src))
+    return sorted(names)
 
 
 def test_every_declared_symbol_is_exported(lib):
