@@ -443,8 +443,6 @@ int alloc_query_state(ahpp_graph* g) {
   s.t_a = (float*)g->alloc(4ull * std::max(nA, 1u));
   s.t_a2 = (float*)g->alloc(4ull * std::max(nA, 1u));
   s.list_u = (uint32_t*)g->alloc(4ull * nU);
-  s.list_v = (uint32_t*)g->alloc(4ull * std::max(nV, 1u));
-  s.list_a = (uint32_t*)g->alloc(4ull * std::max(nA, 1u));
   s.split_acc = (float*)g->alloc(4ull * std::max(g->n_split1, 1u));
   s.split_cnt = (uint32_t*)g->alloc(4ull * std::max(g->n_split1, 1u));
   s.ctl = (QCtl*)g->alloc(sizeof(QCtl));

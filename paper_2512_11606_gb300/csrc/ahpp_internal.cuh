@@ -125,7 +125,6 @@ struct RAcc {
   unsigned long long marked_deg;   // sum of |N(u)| + |A(u)| over marked nodes
   unsigned long long np_flush;     // sum of |N(v)| (r(v) > 0) + |A^-1(a)| (r(a) > 0)
   double sum_r;              // sum_u r_U after the round (pull rounds)
-  uint32_t n_list_v, n_list_a;     // push rounds: touched V / A lists
   uint32_t n_list_u;               // push rounds: marked list length
   uint32_t pad;
   // APP(S): max_u r(u) / (|N(u)| + |A(u)|) after the round (float bits) and

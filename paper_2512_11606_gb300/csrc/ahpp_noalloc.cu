@@ -62,8 +62,6 @@ size_t carve(const ahpp_graph* g, char* base, Q1State* s) {
   s->t_a = (float*)take(4 * na);
   s->t_a2 = (float*)take(4 * na);
   s->list_u = (uint32_t*)take(4 * nu);
-  s->list_v = (uint32_t*)take(4 * nv);
-  s->list_a = (uint32_t*)take(4 * na);
   s->split_acc = (float*)take(4 * ns);
   s->split_cnt = (uint32_t*)take(4 * ns);
   s->ctl = (QCtl*)take(sizeof(QCtl));

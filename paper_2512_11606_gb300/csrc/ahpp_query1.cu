@@ -4,8 +4,11 @@
 // A round is either
 //   * a push round (small frontier): U-push of the marked list with atomic
 //     scatter into t_V / t_A (the U-push of Algorithm 3), then the flush of
-//     every touched V node and attribute (its V and attribute steps) into
-//     r_U, then the selection of the next frontier (warp-ballot compaction);
+//     every V node and attribute with a positive t value (its V and attribute
+//     steps) into r_U, in the work items of the pull phase 1 (long rows split
+//     into chunks over warps, so a hub's flush is spread over the grid), then
+//     the selection of the next frontier (warp-ballot compaction) and the
+//     clearing of t_V / t_A;
 //   * a pull round (large frontier, the synchronous sweep of Algorithm 4):
 //     phase 1 gathers t_V / t_A from the marked residues over V->U and A->U
 //     adjacency, phase 2 gathers r_U' over U->V and U->A adjacency, applies
@@ -340,7 +343,7 @@ __device__ void phase2(const Ctx& c, double theta, bool per_node, Partials& part
 // --------------------------------------------------------- push (sparse)
 
 template <typename WA>
-__device__ void push_u(const Ctx& c, uint32_t n_list, RAcc* acc) {
+__device__ void push_u(const Ctx& c, uint32_t n_list) {
   const DevGraph& g = c.g;
   const uint32_t lane = lane_id();
   for (uint32_t i = c.gw; i < n_list; i += c.nw) {
@@ -360,70 +363,81 @@ __device__ void push_u(const Ctx& c, uint32_t n_list, RAcc* acc) {
         c.s.pi[u] += add;
       }
     }
+    // non-returning reductions: the flush finds the rows it must move by
+    // their value, so no first-touch list is kept
     const uint32_t b1 = g.uv_off[u], e1 = g.uv_off[u + 1];
-    for (uint32_t k0 = b1; k0 < e1; k0 += 32) {
-      const uint32_t k = k0 + lane;
-      const bool ok = k < e1;
-      uint32_t v = 0;
-      bool first = false;
-      if (ok) {
-        v = g.uv_idx[k];
-        first = atomicAdd(&c.s.t_v[v], g.uv_c[k] * p) == 0.f;
-      }
-      warp_append(first, v, c.s.list_v, &acc->n_list_v);
-    }
+    for (uint32_t k = b1 + lane; k < e1; k += 32) atomicAdd(&c.s.t_v[g.uv_idx[k]], g.uv_c[k] * p);
     const float ka = g.k_attr * g.rnorm_u[u] * p;
     const uint32_t b2 = g.ua_off[u], e2 = g.ua_off[u + 1];
-    for (uint32_t k0 = b2; k0 < e2; k0 += 32) {
-      const uint32_t k = k0 + lane;
-      const bool ok = k < e2;
-      uint32_t a = 0;
-      bool first = false;
-      if (ok) {
-        a = g.ua_idx[k];
-        first = atomicAdd(&c.s.t_a[a], wload<WA>(g.ua_w, k) * ka * g.cnorm_a[a]) == 0.f;
-      }
-      warp_append(first, a, c.s.list_a, &acc->n_list_a);
+    for (uint32_t k = b2 + lane; k < e2; k += 32) {
+      const uint32_t a = g.ua_idx[k];
+      atomicAdd(&c.s.t_a[a], wload<WA>(g.ua_w, k) * ka * g.cnorm_a[a]);
     }
   }
 }
 
+// One V (or attribute) row's flush over entries [b, e): r_U[j] += w t for its
+// U neighbours j (returning atomics: the new residues feed max r_U).
 template <typename WA, bool APPS>
-__device__ void flush_va(const Ctx& c, uint32_t nv, uint32_t na, Partials& part) {
+__device__ __forceinline__ void flush_row(const Ctx& c, bool is_a, uint32_t b, uint32_t e, float t,
+                                          Partials& part) {
+  const DevGraph& g = c.g;
+  const uint32_t* idx = is_a ? g.au_idx : g.vu_idx;
+  for (uint32_t k = b + lane_id(); k < e; k += 32) {
+    const float w = is_a ? wload<WA>(g.au_w, k) : g.vu_w[k];
+    const float add = w * t;
+    const uint32_t j = idx[k];
+    const float old = atomicAdd(&c.s.r_u[j], add);
+    part.max_r = fmaxf(part.max_r, old + add);
+    // APP(S): a node's last update sees its new residue (counts of nodes
+    // above threshold may repeat a node; only zero is tested)
+    if (APPS)
+      app_stats(c, old + add, (g.uv_off[j + 1] - g.uv_off[j]) + (g.ua_off[j + 1] - g.ua_off[j]), part);
+  }
+}
+
+// The V and attribute flush of a push round, over the work items of phase 1:
+// a short-row item's rows with t > 0 are flushed one after another by the
+// warp; a long row's chunk by the warp that owns the chunk.  t_V / t_A are
+// only read here (select_frontier clears them after the barrier).
+template <typename WA, bool APPS>
+__device__ void flush_va(const Ctx& c, Partials& part) {
   const DevGraph& g = c.g;
   const uint32_t lane = lane_id();
-  for (uint32_t i = c.gw; i < nv + na; i += c.nw) {
-    const bool is_a = i >= nv;
-    const uint32_t x = is_a ? c.s.list_a[i - nv] : c.s.list_v[i];
-    float* t = is_a ? c.s.t_a : c.s.t_v;
-    float val = 0.f;
-    if (lane == 0) val = t[x];
-    val = __shfl_sync(0xffffffffu, val, 0);
+  const uint32_t nv = g.s1_v.n_items, total = nv + g.s1_a.n_items;
+  for (uint32_t it = c.gw; it < total; it += c.nw) {
+    const bool is_a = it >= nv;
+    const uint4 item = is_a ? g.s1_a.items[it - nv] : g.s1_v.items[it];
     const uint32_t* off = is_a ? g.au_off : g.vu_off;
-    const uint32_t* idx = is_a ? g.au_idx : g.vu_idx;
-    const uint32_t b = off[x], e = off[x + 1];
-    if (lane == 0) {
-      t[x] = 0.f;
-      part.np_flush += e - b;
-    }
-    for (uint32_t k = b + lane; k < e; k += 32) {
-      const float w = is_a ? wload<WA>(g.au_w, k) : g.vu_w[k];
-      const float add = w * val;
-      const uint32_t j = idx[k];
-      const float old = atomicAdd(&c.s.r_u[j], add);
-      part.max_r = fmaxf(part.max_r, old + add);
-      // APP(S): a node's last update sees its new residue (counts of nodes
-      // above threshold may repeat a node; only zero is tested)
-      if (APPS)
-        app_stats(c, old + add, (g.uv_off[j + 1] - g.uv_off[j]) + (g.ua_off[j + 1] - g.ua_off[j]), part);
+    const float* t = is_a ? c.s.t_a : c.s.t_v;
+    if (item.y & (kItemLong | kItemSplit)) {
+      const uint32_t row = item.x;
+      const float tv = t[row];
+      if (!(tv > 0.f)) continue;
+      const uint32_t b = off[row];
+      if (item.z == 0 && lane == 0) part.np_flush += off[row + 1] - b;
+      flush_row<WA, APPS>(c, is_a, b + item.z, b + item.w, tv, part);
+    } else {
+      const uint32_t r0 = item.x, nr = item.y;
+      const float mine = lane < nr ? t[r0 + lane] : 0.f;
+      for (unsigned m = __ballot_sync(0xffffffffu, mine > 0.f); m; m &= m - 1) {
+        const uint32_t r = __ffs(m) - 1;
+        const float tv = __shfl_sync(0xffffffffu, mine, r);
+        const uint32_t b = off[r0 + r], e = off[r0 + r + 1];
+        if (lane == 0) part.np_flush += e - b;
+        flush_row<WA, APPS>(c, is_a, b, e, tv, part);
+      }
     }
   }
 }
 
-// Marking of the next frontier in a push round: r_U > th (per_node: th * cnt(u)).
+// Marking of the next frontier in a push round: r_U > th (per_node: th * cnt(u)),
+// and the clearing of t_V / t_A for the next round's U-push.
 __device__ void select_frontier(const Ctx& c, double theta, bool per_node, RAcc* acc,
                                 Partials& part) {
   const DevGraph& g = c.g;
+  for (uint32_t v = c.gt; v < g.n_v; v += c.nt) c.s.t_v[v] = 0.f;
+  for (uint32_t a = c.gt; a < g.n_a; a += c.nt) c.s.t_a[a] = 0.f;
   const uint32_t n = g.n_u;
   // every warp iterates the same number of times so the ballot is warp-uniform
   const uint32_t span = (n + 31) / 32 * 32;
@@ -550,10 +564,9 @@ k_query1(const __grid_constant__ DevGraph g, const __grid_constant__ Q1State s,
     const double theta = (phase == kPhaseSync && !per_node) ? 0.0 : p.eps_f;
 
     if (!dense) {
-      push_u<WA>(c, marked, A);
+      push_u<WA>(c, marked);
       if (!grid_sync(s.bar, nb)) { status = kStatusWait; break; }
-      const uint32_t nv = __ldcg(&A->n_list_v), na = __ldcg(&A->n_list_a);
-      flush_va<WA, APPS>(c, nv, na, part);
+      flush_va<WA, APPS>(c, part);
       flush_partials<kQ1Warps, APPS>(part, A);
       if (!grid_sync(s.bar, nb)) { status = kStatusWait; break; }
     } else {

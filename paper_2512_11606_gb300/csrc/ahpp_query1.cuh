@@ -19,7 +19,7 @@ struct Q1State {
   float *r_u = nullptr, *pi = nullptr, *pic = nullptr;   // residues (sign = marked), reserves, Kahan
   float *t_v = nullptr, *t_a = nullptr;                  // r(v)/d(v), r(a)/W_col(a)
   float* t_a2 = nullptr;                                 // the other t_A buffer (attribute push)
-  uint32_t *list_u = nullptr, *list_v = nullptr, *list_a = nullptr;   // push-round lists
+  uint32_t* list_u = nullptr;                            // push rounds: the marked list
   float* split_acc = nullptr;                            // partial sums of split rows
   uint32_t* split_cnt = nullptr;                         // finished chunks of split rows
   QCtl* ctl = nullptr;
