@@ -280,11 +280,13 @@ def gpu_index(local_rank):
 
 
 def measured_peak():
+    """HBM peak (GB/s) and where it came from: the measured copy bandwidth of
+    MEASURED_PEAKS.json, else the profiling recipe's fallback of 6.8 TB/s."""
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
-            return float(json.load(f)["hbm_gbs"]), "measured"
+            return float(json.load(f)["hbm_gbs"]), "measured hbm_gbs (MEASURED_PEAKS.json)"
     except Exception:
-        return 6800.0, "fallback"
+        return 6800.0, "fallback 6.8 TB/s (no MEASURED_PEAKS.json)"
 
 
 # ------------------------------------------------------------ byte model
@@ -593,7 +595,7 @@ def run_ours(args, rank, world, local_rank):
                              "traffic": ncu_traffic("k_query1", args.graph, statistics.mean(p_dense)),
                              "traffic_note": ("ncu DRAM bytes per pull round of one query "
                                               "(profiles/k_query1_medium.md) x the mean pull rounds"),
-                             "peak_source": f"{peak_kind_p} hbm_gbs (MEASURED_PEAKS.json)"}
+                             "peak_source": peak_kind_p}
 
     # serving: open-loop Poisson arrivals on the same graph (continuous batching)
     served = None
@@ -631,7 +633,7 @@ def run_ours(args, rank, world, local_rank):
             "traffic_note": ("ncu dram__bytes_read.sum + dram__bytes_write.sum of one 32-query tile "
                              "per tile-round (profiles/k_tiles_medium_tile32.md), scaled by the launch's "
                              "tile-rounds"),
-            "peak_source": f"{peak_kind} hbm_gbs (MEASURED_PEAKS.json)",
+            "peak_source": peak_kind,
             "kernel": "k_tiles (persistent: all rounds + top-k of one 1,024-query step)",
             "algorithmic_bytes_per_launch": alg,
             "tile_rounds_per_launch": tile_rounds}
