@@ -54,6 +54,8 @@ def parse(argv=None):
     ap.add_argument("--graph", default="medium", choices=["medium", "tiny", "large"])
     ap.add_argument("--scale", type=float, default=1.0,
                     help="large graph only: scale |U|, |V|, |E| and |A| by this factor (scalability sweep)")
+    ap.add_argument("--scale-edges-only", action="store_true",
+                    help="with --scale: scale |E| alone (the sweep by edges; nodes unchanged)")
     ap.add_argument("--ablation", type=int, default=3,
                     help="single-query ablation of the ASRP switch rule and APP on N queries (0: off)")
     ap.add_argument("--scale-leg", type=float, default=0.25,
@@ -74,21 +76,22 @@ def parse(argv=None):
     return ap.parse_args(argv)
 
 
-def graph_spec(name, scale=1.0):
+def graph_spec(name, scale=1.0, edges_only=False):
     if name == "large":
-        return synth.scaled(synth.LARGE, scale)
+        return synth.scaled(synth.LARGE, scale, edges_only)
     return dict(synth.MEDIUM_BF16) if name == "medium" else dict(synth.TINY, bf16=True)
 
 
 def workload_config(args, extra=None):
-    spec = graph_spec(args.graph, args.scale)
+    spec = graph_spec(args.graph, args.scale, args.scale_edges_only)
     cfg = {
         "workload": (f"{args.graph} attributed bipartite graph |U|={spec['n_u']:,} |V|={spec['n_v']:,} "
                      f"|E|={spec['n_e']:,} Zipf({spec['gamma_u']}) degrees, |A|={spec['n_a']:,} "
                      f"x{spec['m']} bf16 attribute weights; ASRP (Theorem 3 lambda), "
                      f"alpha={ALPHA}, beta={BETA}, eps={args.eps:g}, top-{args.k}; "
                      f"{args.batch} queries per step (batched persistent launch)"),
-        "graph": args.graph if args.scale == 1.0 else f"{args.graph} x{args.scale:g}",
+        "graph": (args.graph if args.scale == 1.0 else
+                  f"{args.graph} x{args.scale:g}{' edges only' if args.scale_edges_only else ''}"),
         "batch_queries_per_gpu": args.batch,
         "eps": args.eps,
         "k": args.k,
@@ -468,7 +471,7 @@ def run_ours(args, rank, world, local_rank):
     import torch
     from paper_2512_11606_gb300 import ahpp
 
-    spec = graph_spec(args.graph, args.scale)
+    spec = graph_spec(args.graph, args.scale, args.scale_edges_only)
     g = synth.make_graph(**spec)
 
     cpu = None
@@ -1037,7 +1040,7 @@ def run_reference(args, rank, world):
     """The reference arm: the FP64 CPU oracle on the host cores."""
     if rank != 0:
         return None
-    spec = graph_spec(args.graph, args.scale)
+    spec = graph_spec(args.graph, args.scale, args.scale_edges_only)
     g = synth.make_graph(**spec)
     n = args.cpu_queries or min(16, host_cores())
     import oracle

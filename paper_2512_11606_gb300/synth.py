@@ -116,13 +116,14 @@ def _merge_runs(runs: list) -> np.ndarray:
     return runs[0] if len(runs) == 1 else np.sort(np.concatenate(runs), kind="stable")
 
 
-def scaled(spec: dict, factor: float) -> dict:
+def scaled(spec: dict, factor: float, edges_only: bool = False) -> dict:
     """A workload shape with |U|, |V|, |E| and |A| scaled by factor (the
     attributes per node, exponents, weight laws and seed unchanged): the
-    scalability sweep's graphs and the reduced large graph of the tests."""
+    scalability sweep's graphs and the reduced large graph of the tests.
+    edges_only scales |E| alone (the sweep by edges: same nodes, sparser)."""
     out = dict(spec)
     if factor != 1.0:
-        for key in ("n_u", "n_v", "n_e", "n_a"):
+        for key in (("n_e",) if edges_only else ("n_u", "n_v", "n_e", "n_a")):
             out[key] = max(1, int(round(out[key] * factor)))
     return out
 
