@@ -353,17 +353,23 @@ def topk_bytes(info, queries):
 # any of them changes (comments and layout aside) the figure no longer
 # applies and ncu_traffic returns None.
 NCU_TRAFFIC = {
+    # ncu --set full of one 32-query tile on the medium graph (106 tile-rounds):
+    # profiles/k_tiles_medium_tile32.md
     "k_tiles": {
         "graph": "medium",
-        "bytes_per_unit": None,              # dram__bytes_read.sum + dram__bytes_write.sum per tile-round
-        "l2_to_sm_bytes_per_unit": None,     # l1tex__m_xbar2l1tex_read_bytes.sum per tile-round
-        "sources": {},
+        "bytes_per_unit": 2.424642e9,        # dram__bytes_read.sum + dram__bytes_write.sum per tile-round
+        "l2_to_sm_bytes_per_unit": 8.972795e9,   # l1tex__m_xbar2l1tex_read_bytes.sum per tile-round
+        "sources": {"ahpp_batch_kernel.cuh": "f341ce418086809a", "ahpp_batch.cu": "f92167d838a2d532",
+                    "ahpp_batch.cuh": "2f7f8c2bb4bfbcdd", "ahpp_internal.cuh": "45194dba8b4be444"},
     },
+    # the same capture's third k_query1 launch, one plain query (105 pull rounds):
+    # profiles/k_query1_medium.md
     "k_query1": {
         "graph": "medium",
-        "bytes_per_unit": None,              # per pull round
-        "l2_to_sm_bytes_per_unit": None,
-        "sources": {},
+        "bytes_per_unit": 5.008213e8,        # per pull round
+        "l2_to_sm_bytes_per_unit": 1.402732e9,
+        "sources": {"ahpp_query1.cu": "90fefeb4b00d7cd3", "ahpp_query1.cuh": "e356ae0e412d9385",
+                    "ahpp_internal.cuh": "45194dba8b4be444"},
     },
 }
 
