@@ -127,3 +127,17 @@ def test_code_digest_ignores_comments_and_layout_only():
     assert bench.code_digest(src) != bench.code_digest(src.replace("x + 1", "x + 2"))
     assert bench.code_digest(src) != bench.code_digest(src.replace('"a // b"', '"a /* b"'))
     assert bench.code_digest("char c = '\\'';") != bench.code_digest("char c = '\\\\';")
+
+
+def test_scaled_workloads_of_the_sweep():
+    """The sweep's graphs: by nodes and edges (every size scaled, shapes kept)
+    or by edges alone (same nodes, sparser), and the large recipe at F = 1."""
+    from paper_2512_11606_gb300 import synth
+    both = bench.graph_spec("large", 0.25)
+    assert (both["n_u"], both["n_v"], both["n_e"], both["n_a"]) == (1_250_000, 1_250_000, 50_000_000, 12_500)
+    edges = bench.graph_spec("large", 0.25, edges_only=True)
+    assert (edges["n_u"], edges["n_v"], edges["n_e"], edges["n_a"]) == (5_000_000, 5_000_000, 50_000_000, 50_000)
+    for spec in (both, edges):
+        assert {k: spec[k] for k in ("m", "gamma_u", "gamma_v", "seed", "bf16")} == \
+               {k: synth.LARGE[k] for k in ("m", "gamma_u", "gamma_v", "seed", "bf16")}
+    assert bench.graph_spec("large") == synth.LARGE
