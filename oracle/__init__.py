@@ -52,6 +52,13 @@ class _Stats(ctypes.Structure):
                 ("leak", ctypes.c_double), ("max_resid", ctypes.c_double)]
 
 
+class _PushState(ctypes.Structure):
+    """Where a resumable push stands between rounds (og_push_state)."""
+    _fields_ = [("round", ctypes.c_uint32), ("sync", ctypes.c_uint32),
+                ("switch_round", ctypes.c_uint32), ("pad", ctypes.c_uint32),
+                ("n_p", ctypes.c_uint64), ("pushes", ctypes.c_uint64), ("leak", ctypes.c_double)]
+
+
 class _Trace(ctypes.Structure):
     _fields_ = [("cap", ctypes.c_uint32), ("frontier", _u64p), ("n_p", _u64p),
                 ("max_r", _f64p), ("sum_r", _f64p), ("sum_pi", _f64p), ("phase", _u8p)]
@@ -81,6 +88,11 @@ def lib() -> ctypes.CDLL:
                               ctypes.c_uint32, ctypes.c_double, ctypes.c_double, ctypes.c_int,
                               ctypes.c_uint32, _f64p, _f64p, ctypes.POINTER(_Stats),
                               ctypes.POINTER(_Trace)]
+        L.og_push_start.argtypes = [ctypes.c_void_p, ctypes.c_uint32, _f64p, _f64p,
+                                    ctypes.POINTER(_PushState)]
+        L.og_push_resume.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_double, ctypes.c_double,
+                                     ctypes.c_double, ctypes.c_double, ctypes.c_int, ctypes.c_uint32,
+                                     _f64p, _f64p, ctypes.POINTER(_PushState), ctypes.POINTER(_Stats)]
         L.og_forward_push.argtypes = [ctypes.c_void_p, ctypes.c_double, ctypes.c_double,
                                       ctypes.c_uint32, ctypes.c_double, ctypes.c_uint64,
                                       _f64p, _f64p, ctypes.POINTER(_Stats)]
@@ -195,6 +207,30 @@ class OracleGraph:
         trace = {k: v[:n].copy() for k, v in buf.items()}
         return PushResult(pi, r_u, rc, stats, trace)
 
+    def push_start(self, q: int) -> "ResumablePush":
+        """The initial state of a push from q (unit residue at q), to be
+        advanced by push_resume a few rounds at a time."""
+        r = ResumablePush(np.zeros(self.n_u), np.zeros(self.n_u), _PushState())
+        rc = lib().og_push_start(self._h, q, _p(r.pi, _f64p), _p(r.r_u, _f64p), ctypes.byref(r.state))
+        if rc < 0:
+            raise ValueError(f"oracle push start failed ({rc})")
+        return r
+
+    def push_resume(self, r: "ResumablePush", algo: str, alpha: float, beta: float, eps: float,
+                    lam: float | None = None, switch_rule: int = 0, rounds: int = 1) -> int:
+        """At most `rounds` more rounds of the push in r (updated in place);
+        returns 0 once converged, 1 if rounds ran out first.  Its stats hold
+        the totals so far."""
+        st = _Stats()
+        rc = lib().og_push_resume(self._h, ALGOS[algo], alpha, beta, eps,
+                                  0.0 if lam is None else float(lam), switch_rule, rounds,
+                                  _p(r.pi, _f64p), _p(r.r_u, _f64p), ctypes.byref(r.state),
+                                  ctypes.byref(st))
+        if rc < 0:
+            raise ValueError(f"oracle push resume failed ({rc})")
+        r.stats = {f: getattr(st, f) for f, _ in _Stats._fields_}
+        return rc
+
     def forward_push(self, alpha: float, beta: float, q: int, eps: float,
                      max_pushes: int = 1 << 40) -> PushResult:
         """Algorithm 2 (FIFO order)."""
@@ -207,6 +243,15 @@ class OracleGraph:
             raise ValueError(f"oracle forward push failed ({rc})")
         stats = {f: getattr(st, f) for f, _ in _Stats._fields_}
         return PushResult(pi, r_u, rc, stats, {})
+
+
+@dataclass
+class ResumablePush:
+    """Reserves, residues and round state of a push advanced in pieces."""
+    pi: np.ndarray
+    r_u: np.ndarray
+    state: _PushState
+    stats: dict | None = None
 
 
 def topk(score: np.ndarray, k: int):

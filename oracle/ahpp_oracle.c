@@ -348,6 +348,110 @@ static void og_sums(const og_graph *g, const double *r_u, const double *pi,
     *max_r = m; *sum_r = s; *sum_pi = p;
 }
 
+/* Where a push run stands between two rounds: everything besides the
+ * residues and reserves that the next round depends on. */
+typedef struct {
+    uint32_t round;           /* rounds run so far */
+    uint32_t sync;            /* ASRP / APP(S): the synchronous phase has begun */
+    uint32_t switch_round;    /* first synchronous round (0 = not switched) */
+    uint32_t pad;
+    uint64_t n_p;             /* Algorithm 4's push counter so far */
+    uint64_t pushes;          /* U-node pushes so far */
+    double leak;              /* mass dropped at dangling rows so far */
+} og_push_state;
+
+static int og_push_args_ok(const og_graph *g, int algo, double alpha, double beta, double eps,
+                           double lambda) {
+    return (alpha > 0.0 && alpha < 1.0) && (beta >= 0.0 && beta <= 1.0) && (eps > 0.0) &&
+           (algo == OG_APP || algo == OG_ASRP || algo == OG_APPS) &&
+           !(algo == OG_ASRP && !(lambda > 0.0)) && g != NULL;
+}
+
+/* Rounds of APP / ASRP / APP(S) from the state (pi, r_u, *ps) until the loop
+ * test of Algorithms 3 and 4 fails (OG_OK) or ps->round reaches round_cap
+ * (OG_ENOTCONVERGED).  pi and r_u are updated in place; the trace, if given,
+ * records the rounds by their index. */
+static int og_push_run(const og_graph *g, int algo, double alpha, double beta, double eps,
+                       double lambda, int switch_rule, uint32_t round_cap, double *pi, double *r_u,
+                       og_push_state *ps, og_trace *tr) {
+    int app_thr = algo == OG_APP || algo == OG_APPS;    /* APP's per-node thresholds */
+    uint32_t n = g->n_u;
+    double *r_v = calloc(g->n_v ? g->n_v : 1, sizeof(double));
+    double *r_a = calloc(g->n_a ? g->n_a : 1, sizeof(double));
+    uint32_t *sel = malloc((n ? n : 1) * sizeof(uint32_t));
+    uint32_t *cnt = malloc((n ? n : 1) * sizeof(uint32_t));
+    if (!r_v || !r_a || !sel || !cnt) {
+        free(r_v); free(r_a); free(sel); free(cnt); return OG_ENOMEM;
+    }
+    for (uint32_t u = 0; u < n; u++)
+        cnt[u] = (uint32_t)((g->uv.off[u + 1] - g->uv.off[u]) + (g->ua.off[u + 1] - g->ua.off[u]));
+    double EE = (double)(g->uv.nnz + g->ua.nnz);
+    double r_max = eps / EE;                        /* APP threshold scale */
+    double eps_f = (algo == OG_ASRP) ? eps / lambda : 0.0;
+    double lg = log(1.0 / (1.0 - alpha));
+    int rc = OG_OK;
+    for (;;) {
+        /* loop test of Algorithms 3 and 4: some U residue above its threshold */
+        int any = 0;
+        for (uint32_t u = 0; u < n && !any; u++) {
+            double th = app_thr ? r_max * (double)cnt[u] : eps_f;
+            if (r_u[u] > th) any = 1;
+        }
+        if (!any) break;
+        if (ps->round >= round_cap) { rc = OG_ENOTCONVERGED; break; }
+        uint64_t nf;
+        if (algo == OG_APP || (algo == OG_APPS && !ps->sync))
+            nf = og_round(g, alpha, beta, cnt, r_max, r_u, r_v, r_a, pi, sel, &ps->n_p, &ps->leak);
+        else if (algo == OG_APPS)
+            nf = og_round(g, alpha, beta, NULL, 0.0, r_u, r_v, r_a, pi, sel, &ps->n_p, &ps->leak);
+        else
+            nf = og_round(g, alpha, beta, NULL, ps->sync ? 0.0 : eps_f, r_u, r_v, r_a, pi, sel,
+                          &ps->n_p, &ps->leak);
+        ps->round++;
+        ps->pushes += nf;
+        double m, s, p;
+        og_sums(g, r_u, pi, &m, &s, &p);
+        if (tr && ps->round <= tr->cap) {
+            tr->frontier[ps->round - 1] = nf;
+            tr->n_p[ps->round - 1] = ps->n_p;
+            tr->max_r[ps->round - 1] = m;
+            tr->sum_r[ps->round - 1] = s;
+            tr->sum_pi[ps->round - 1] = p;
+            tr->phase[ps->round - 1] = (uint8_t)ps->sync;
+        }
+        if (algo == OG_ASRP && !ps->sync) {         /* ASRP's switch test */
+            double budget;
+            if (switch_rule == 1)
+                budget = 2.0 * EE * (log(1.0 / (lambda * m)) / lg);
+            else if (switch_rule == 2)
+                budget = INFINITY;
+            else
+                budget = 2.0 * EE * fmax(0.0, log(m / eps_f) / lg);
+            if ((double)ps->n_p >= budget) { ps->sync = 1; ps->switch_round = ps->round + 1; }
+        }
+        if (algo == OG_APPS && !ps->sync) {         /* APP(S): the same test in APP's units */
+            double mrel = 0.0;
+            for (uint32_t u = 0; u < n; u++)
+                if (cnt[u] > 0 && r_u[u] / (double)cnt[u] > mrel) mrel = r_u[u] / (double)cnt[u];
+            double budget = 2.0 * EE * fmax(0.0, log(mrel / r_max) / lg);
+            if ((double)ps->n_p >= budget) { ps->sync = 1; ps->switch_round = ps->round + 1; }
+        }
+    }
+    free(r_v); free(r_a); free(sel); free(cnt);
+    return rc;
+}
+
+static void og_push_stats(const og_graph *g, const og_push_state *ps, const double *r_u,
+                          const double *pi, og_stats *st) {
+    memset(st, 0, sizeof(*st));
+    st->rounds = ps->round;
+    st->switch_round = ps->switch_round;
+    st->n_p = ps->n_p;
+    st->pushes = ps->pushes;
+    st->leak = ps->leak;
+    og_sums(g, r_u, pi, &st->max_resid, &st->resid_sum, &st->reserve_sum);
+}
+
 /*
  * APP (Algorithm 3), ASRP (Algorithm 4) or APP(S) (Exp-2) from source q.
  *   eps: error threshold; lambda: ASRP's parameter (eps_f = eps / lambda);
@@ -359,87 +463,46 @@ static void og_sums(const og_graph *g, const double *r_u, const double *pi,
 int og_push(const og_graph *g, int algo, double alpha, double beta, uint32_t q,
             double eps, double lambda, int switch_rule, uint32_t max_rounds,
             double *pi, double *r_u_out, og_stats *st, og_trace *tr) {
-    if (q >= g->n_u || !(alpha > 0.0 && alpha < 1.0) || !(beta >= 0.0 && beta <= 1.0) ||
-        !(eps > 0.0) || (algo != OG_APP && algo != OG_ASRP && algo != OG_APPS) ||
-        (algo == OG_ASRP && !(lambda > 0.0)))
-        return OG_EINVAL;
-    int app_thr = algo == OG_APP || algo == OG_APPS;    /* APP's per-node thresholds */
+    if (!og_push_args_ok(g, algo, alpha, beta, eps, lambda) || q >= g->n_u) return OG_EINVAL;
     uint32_t n = g->n_u;
     double *r_u = calloc(n ? n : 1, sizeof(double));
-    double *r_v = calloc(g->n_v ? g->n_v : 1, sizeof(double));
-    double *r_a = calloc(g->n_a ? g->n_a : 1, sizeof(double));
-    uint32_t *sel = malloc((n ? n : 1) * sizeof(uint32_t));
-    uint32_t *cnt = malloc((n ? n : 1) * sizeof(uint32_t));
-    if (!r_u || !r_v || !r_a || !sel || !cnt) {
-        free(r_u); free(r_v); free(r_a); free(sel); free(cnt); return OG_ENOMEM;
-    }
+    if (!r_u) return OG_ENOMEM;
     memset(pi, 0, n * sizeof(double));
-    memset(st, 0, sizeof(*st));
-    for (uint32_t u = 0; u < n; u++)
-        cnt[u] = (uint32_t)((g->uv.off[u + 1] - g->uv.off[u]) + (g->ua.off[u + 1] - g->ua.off[u]));
     r_u[q] = 1.0;                                   /* unit residue at the source */
-    double EE = (double)(g->uv.nnz + g->ua.nnz);
-    double r_max = eps / EE;                        /* APP threshold scale */
-    double eps_f = (algo == OG_ASRP) ? eps / lambda : 0.0;
-    double lg = log(1.0 / (1.0 - alpha));
-    int sync = 0;
-    uint64_t n_p = 0;
-    double leak = 0.0;
-    int rc = OG_OK;
-    uint32_t round = 0;
-    for (;;) {
-        /* loop test of Algorithms 3 and 4: some U residue above its threshold */
-        int any = 0;
-        for (uint32_t u = 0; u < n && !any; u++) {
-            double th = app_thr ? r_max * (double)cnt[u] : eps_f;
-            if (r_u[u] > th) any = 1;
-        }
-        if (!any) break;
-        if (round >= max_rounds) { rc = OG_ENOTCONVERGED; break; }
-        uint64_t nf;
-        if (algo == OG_APP || (algo == OG_APPS && !sync))
-            nf = og_round(g, alpha, beta, cnt, r_max, r_u, r_v, r_a, pi, sel, &n_p, &leak);
-        else if (algo == OG_APPS)
-            nf = og_round(g, alpha, beta, NULL, 0.0, r_u, r_v, r_a, pi, sel, &n_p, &leak);
-        else
-            nf = og_round(g, alpha, beta, NULL, sync ? 0.0 : eps_f, r_u, r_v, r_a, pi, sel,
-                          &n_p, &leak);
-        round++;
-        st->pushes += nf;
-        double m, s, p;
-        og_sums(g, r_u, pi, &m, &s, &p);
-        if (tr && round <= tr->cap) {
-            tr->frontier[round - 1] = nf;
-            tr->n_p[round - 1] = n_p;
-            tr->max_r[round - 1] = m;
-            tr->sum_r[round - 1] = s;
-            tr->sum_pi[round - 1] = p;
-            tr->phase[round - 1] = (uint8_t)sync;
-        }
-        if (algo == OG_ASRP && !sync) {             /* ASRP's switch test */
-            double budget;
-            if (switch_rule == 1)
-                budget = 2.0 * EE * (log(1.0 / (lambda * m)) / lg);
-            else if (switch_rule == 2)
-                budget = INFINITY;
-            else
-                budget = 2.0 * EE * fmax(0.0, log(m / eps_f) / lg);
-            if ((double)n_p >= budget) { sync = 1; st->switch_round = round + 1; }
-        }
-        if (algo == OG_APPS && !sync) {             /* APP(S): the same test in APP's units */
-            double mrel = 0.0;
-            for (uint32_t u = 0; u < n; u++)
-                if (cnt[u] > 0 && r_u[u] / (double)cnt[u] > mrel) mrel = r_u[u] / (double)cnt[u];
-            double budget = 2.0 * EE * fmax(0.0, log(mrel / r_max) / lg);
-            if ((double)n_p >= budget) { sync = 1; st->switch_round = round + 1; }
-        }
-    }
-    st->rounds = round;
-    st->n_p = n_p;
-    st->leak = leak;
-    og_sums(g, r_u, pi, &st->max_resid, &st->resid_sum, &st->reserve_sum);
+    og_push_state ps;
+    memset(&ps, 0, sizeof(ps));
+    int rc = og_push_run(g, algo, alpha, beta, eps, lambda, switch_rule, max_rounds, pi, r_u, &ps, tr);
+    if (rc < 0) { free(r_u); return rc; }
+    og_push_stats(g, &ps, r_u, pi, st);
     if (r_u_out) memcpy(r_u_out, r_u, n * sizeof(double));
-    free(r_u); free(r_v); free(r_a); free(sel); free(cnt);
+    free(r_u);
+    return rc;
+}
+
+/*
+ * The same rounds resumed: from the reserves pi, residues r_u and state *ps
+ * a previous og_push_start / og_push_resume left (pi and r_u are updated in
+ * place), at most more_rounds further rounds.  OG_OK once the loop test
+ * fails, OG_ENOTCONVERGED when the rounds ran out first.  A run split into
+ * resumed pieces performs exactly the rounds of one uninterrupted og_push.
+ */
+int og_push_start(const og_graph *g, uint32_t q, double *pi, double *r_u, og_push_state *ps) {
+    if (!g || q >= g->n_u) return OG_EINVAL;
+    memset(pi, 0, g->n_u * sizeof(double));
+    memset(r_u, 0, g->n_u * sizeof(double));
+    r_u[q] = 1.0;                                   /* unit residue at the source */
+    memset(ps, 0, sizeof(*ps));
+    return OG_OK;
+}
+
+int og_push_resume(const og_graph *g, int algo, double alpha, double beta, double eps,
+                   double lambda, int switch_rule, uint32_t more_rounds, double *pi, double *r_u,
+                   og_push_state *ps, og_stats *st) {
+    if (!og_push_args_ok(g, algo, alpha, beta, eps, lambda) || !ps) return OG_EINVAL;
+    uint32_t cap = ps->round + more_rounds < ps->round ? UINT32_MAX : ps->round + more_rounds;
+    int rc = og_push_run(g, algo, alpha, beta, eps, lambda, switch_rule, cap, pi, r_u, ps, NULL);
+    if (rc < 0) return rc;
+    if (st) og_push_stats(g, ps, r_u, pi, st);
     return rc;
 }
 

@@ -557,3 +557,21 @@ def test_forward_push_fifo_hand_trace():
     assert res.rc == 0 and res.stats["pushes"] == int(fx.kv["fp_pushes"][0])
     assert list(res.pi) == [float(x) for x in fx.kv["fp_pi"]]          # dyadic: exact in FP64
     assert list(res.r_u) == [float(x) for x in fx.kv["fp_r"]]
+
+
+@pytest.mark.parametrize("algo", ["asrp", "app", "apps"])
+def test_push_resumed_in_pieces_is_the_same_run(tiny, algo):
+    """A push advanced a few rounds at a time from a kept state (the bounded
+    steps of the bench's CPU arm) performs exactly the rounds of one
+    uninterrupted run: identical reserves, residues and counters."""
+    og, q, lam = tiny["og"], tiny["q"], tiny["lam"]
+    whole = og.push(algo, ALPHA, BETA, q, 1e-6, lam=lam)
+    r = og.push_start(q)
+    rc, pieces = 1, 0
+    while rc == 1:
+        rc = og.push_resume(r, algo, ALPHA, BETA, 1e-6, lam=lam, rounds=3)
+        pieces += 1
+    assert rc == 0 and pieces > 3
+    assert np.array_equal(r.pi, whole.pi) and np.array_equal(r.r_u, whole.r_u)
+    for key in ("rounds", "switch_round", "n_p", "pushes", "leak", "reserve_sum", "resid_sum"):
+        assert r.stats[key] == whole.stats[key], key
