@@ -1,6 +1,6 @@
 """Parity at the full workload sizes, in the launch configuration bench.py times.
 
-Every comparison below holds the spec bar: each score within 1e-6
+Every comparison below holds the parity bar: each score within 1e-6
 absolute of the FP64 oracle push at every eps, within eps of exact AHPP
 (Theorem 2) up to FP32 rounding, and top-k overlap >= 0.99 under the 2 eps
 tie rule.  The oracle references (pushes, and exact AHPP by Algorithm 1 run
