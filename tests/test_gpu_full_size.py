@@ -11,8 +11,10 @@ Medium (|U|=1M, |V|=500k, |E|=20M, |A|=10k x 20, bf16 attribute weights):
 the single-query path and a 64-query batched launch element by element
 against the oracle push; Theorem 2 against the oracle's exact AHPP; the
 1,024-query launch bench.py times; the single-query workload's other eps;
-and continuous batching with the serving workload's request mix, every
-sampled request against the same query alone and against the oracle.
+the ablation arms of Exp-2 (APP, APP(S), APP(E), the printed switch rule)
+against the oracle run with the same rule; and continuous batching with the
+serving workload's request mix, every sampled request against the same
+query alone and against the oracle.
 
 Large, reduced (the large recipe with |U|, |V|, |E|, |A| scaled by 1/4:
 1.25M / 1.25M / 50M edges, 12,500 x 30 attributes, Zipf(2.0)): one query
@@ -51,6 +53,8 @@ _rng = np.random.default_rng(17)
 SERVE_EPS = np.exp(_rng.uniform(np.log(1e-7), np.log(1e-4), SERVE_N))
 SERVE_K = _rng.choice([10, 100, 1000], SERVE_N)
 SERVE_CHECK = [0, 5, 23, 24, 30, 47]
+# the ablation arms of Exp-2 at full size: (oracle algo, library algo name, switch rule)
+ARMS = [("app", "AHPP_APP", 0), ("apps", "AHPP_APP_S", 0), ("asrp", "AHPP_ASRP", 2), ("asrp", "AHPP_ASRP", 1)]
 
 
 @pytest.fixture(scope="module")
@@ -84,6 +88,7 @@ def medium(ahpp):
              ("exact0", pi_job(Q1024[0], T_EXACT)), ("exact63", pi_job(Q1024[63], T_EXACT))]
     named += [(f"other{e:g}", push_job(Q_OTHER, e, lam)) for e in OTHER_EPS]
     named += [(f"serve{i}", push_job(SERVE_Q[i], SERVE_EPS[i], lam)) for i in SERVE_CHECK]
+    named += [(f"arm{a}{r}", push_job(Q_OTHER, 1e-6, lam, algo=a, switch_rule=r)) for a, _, r in ARMS]
     refs = Refs(MED, named)
     G = ahpp.Graph.from_arrays(g, lam=lam)
     yield dict(g=g, og=og, lam=lam, G=G, refs=refs)
@@ -147,6 +152,36 @@ def test_medium_single_query_other_eps(medium, eps):
     check_dense(pi, pi_ref)
     assert abs(st["rounds"] - ref_stats["rounds"]) <= 1
     check_topk(top.nodes, top.scores, pi_ref, 100, eps)
+
+
+@pytest.mark.parametrize("arm", ARMS, ids=["app", "apps", "app_e", "asrp_printed_switch"])
+def test_medium_ablation_arms_vs_oracle(ahpp, medium, arm):
+    """The ablation arms of Exp-2 at the medium size: APP, APP(S), APP(E)
+    (ASRP never switching) and ASRP with the switch budget as printed, each
+    through the single-query and the batched launch, every score within 1e-6
+    of the oracle run with the same rule, rounds within one of the oracle's
+    (three for APP, whose stop test is per node)."""
+    oalgo, lib_algo, rule = arm
+    G = ahpp.Graph.from_arrays(medium["g"], lam=medium["lam"], algo=getattr(ahpp, lib_algo),
+                               switch_rule=rule)
+    try:
+        pi, st, rc = G.query_dense(Q_OTHER, 1e-6)
+        dense, stats, rc_b = G.query_batch_dense([Q_OTHER] + Q1024[:7], 1e-6)
+    finally:
+        G.close()
+    assert rc == 0 and rc_b == 0 and st["status"] == 0 and stats[0]["status"] == 0
+    pi_ref, ref_stats = medium["refs"][f"arm{oalgo}{rule}"]
+    check_dense(pi, pi_ref)
+    check_dense(dense[0], pi_ref)
+    # APP stops once every residue is at most r_max (|N(u)| + |A(u)|), about
+    # 1e-12 here: FP32 residues that close to their thresholds (about 1e-7
+    # relative from the oracle's FP64) can keep a node pushing a round or two
+    # longer; the other arms stop on a test that FP32 rounding does not reach
+    # (eps / lambda, about 2.4e-10, or APP(S)'s synchronous sweep of every
+    # residue) and agree within one round
+    tol = 3 if oalgo == "app" else 1
+    assert abs(st["rounds"] - ref_stats["rounds"]) <= tol
+    assert abs(stats[0]["rounds"] - ref_stats["rounds"]) <= tol
 
 
 def test_medium_served_mix_equals_alone(ahpp, medium):
