@@ -68,8 +68,15 @@ def _ref_worker(rank, world, port, out_path):
     args = bench.parse(["--impl", "reference", "--graph", "tiny", "--steps", "1",
                       "--warmup", "3", "--cpu-queries", "2"])
     out = bench.run_reference(args, rank, world)
+    ok = None
+    if out is not None:
+        cb, e2e = out["cpu_baseline"], out["e2e"]
+        ok = (out["value"] > 0 and out["impl"] == "reference" and out["steps"] == 1 and out["warmup"] == 3
+              and cb["kind"] == "oracle" and cb["cores"] == 2 and cb["value"] == out["value"]
+              and "rounds" in cb["sample"] and e2e["value"] == out["value"]
+              and e2e["h2d_bytes_per_step"] == 0 and e2e["d2h_bytes_per_step"] == 0)
     with open(f"{out_path}.{rank}.txt", "w") as f:
-        f.write("none" if out is None else repr(out["value"] > 0 and out["impl"] == "reference"))
+        f.write("none" if out is None else repr(ok))
 
 
 def test_reference_arm_runs_on_rank0_only(tmp_path):
