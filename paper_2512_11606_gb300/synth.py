@@ -104,10 +104,29 @@ def _searchsorted(sorted_a: np.ndarray, v: np.ndarray, right: bool = False) -> n
                               torch.from_numpy(np.ascontiguousarray(v)), right=right).numpy()
 
 
+def _take(a: np.ndarray, idx: np.ndarray) -> np.ndarray:
+    """a[idx] for an integer index array (a gather: one answer)."""
+    import torch
+    return torch.from_numpy(np.ascontiguousarray(a))[torch.from_numpy(np.ascontiguousarray(idx))].numpy()
+
+
 def _sort(a: np.ndarray) -> np.ndarray:
     """np.sort(a)."""
     import torch
     return torch.sort(torch.from_numpy(np.ascontiguousarray(a))).values.numpy()
+
+
+def _sort_rows(a: np.ndarray) -> np.ndarray:
+    """np.sort(a, axis=1) of an integer matrix (integer rows have one sorted order)."""
+    import torch
+    return torch.sort(torch.from_numpy(np.ascontiguousarray(a)), dim=1).values.numpy()
+
+
+def _rows_with_repeats(a: np.ndarray) -> np.ndarray:
+    """Indices of the rows of a row-sorted matrix that hold a value twice."""
+    import torch
+    t = torch.from_numpy(a)
+    return torch.nonzero((t[:, 1:] == t[:, :-1]).any(dim=1)).reshape(-1).numpy()
 
 
 def _merge_runs(runs: list) -> np.ndarray:
@@ -187,8 +206,8 @@ def bipartite_edges(n_u: int, n_v: int, n_e: int, gamma_u: float, gamma_v: float
         need = n_e - count
         draw = max(need + need // 2, 1024)
         if rounds <= 16:
-            eu = su[rng.integers(0, su.shape[0], size=draw)]
-            ev = sv[rng.integers(0, sv.shape[0], size=draw)]
+            eu = _take(su, rng.integers(0, su.shape[0], size=draw))
+            ev = _take(sv, rng.integers(0, sv.shape[0], size=draw))
         else:  # saturated hub pairs: fall back to uniform pairs
             eu = rng.integers(0, n_u, size=draw)
             ev = rng.integers(0, n_v, size=draw)
@@ -198,14 +217,14 @@ def bipartite_edges(n_u: int, n_v: int, n_e: int, gamma_u: float, gamma_v: float
         # order), test membership with sorted needles, and mark the first of
         # each run of equal pairs
         order = _stable_argsort(cand)
-        sc = cand[order]
+        sc = _take(cand, order)
         keep = np.ones(sc.shape[0], dtype=bool)
         for run in runs:
             pos = _searchsorted(run, sc)
             pos[pos == run.shape[0]] = 0
-            keep &= run[pos] != sc
+            keep &= _take(run, pos) != sc
         keep[1:] &= sc[1:] != sc[:-1]
-        cand = cand[_sort(order[keep])][:need]
+        cand = _take(cand, _sort(order[keep]))[:need]
         runs.append(_sort(cand))
         count += cand.shape[0]
     key = _merge_runs(runs)
@@ -213,11 +232,14 @@ def bipartite_edges(n_u: int, n_v: int, n_e: int, gamma_u: float, gamma_v: float
 
 
 def bf16_round(x: np.ndarray) -> np.ndarray:
-    """Round float32 values to the nearest bfloat16 value (ties to even)."""
-    b = np.ascontiguousarray(x, dtype=np.float32).view(np.uint32).astype(np.uint64)
-    lsb = (b >> 16) & 1
-    b = (b + 0x7FFF + lsb) >> 16 << 16
-    return b.astype(np.uint32).view(np.float32)
+    """Round float32 values to the nearest bfloat16 value (ties to even): the
+    bit pattern b becomes (b + 0x7FFF + bit 16 of b) with the low 16 bits
+    cleared, modulo 2^32 (integer arithmetic, on all host cores)."""
+    import torch
+    b = torch.from_numpy(np.ascontiguousarray(x, dtype=np.float32).view(np.int32)).to(torch.int64) & 0xFFFFFFFF
+    b = ((b + 0x7FFF + ((b >> 16) & 1)) >> 16 << 16) & 0xFFFFFFFF
+    b = torch.where(b >= 1 << 31, b - (1 << 32), b).to(torch.int32)
+    return b.numpy().view(np.float32)
 
 
 def node_attributes(n_u: int, n_a: int, m: int, weight_law: str, seed: int,
@@ -238,12 +260,12 @@ def node_attributes(n_u: int, n_a: int, m: int, weight_law: str, seed: int,
             return rng.integers(0, n_a, size=(rows, m))
         return rng.choice(n_a, size=(rows, m), p=p)
 
-    a = np.sort(draw(n_u), axis=1)
-    bad = np.nonzero((a[:, 1:] == a[:, :-1]).any(axis=1))[0]
+    a = _sort_rows(draw(n_u))
+    bad = _rows_with_repeats(a)
     while bad.size:
-        a[bad] = np.sort(draw(bad.size), axis=1)
+        a[bad] = _sort_rows(draw(bad.size))
         sub = a[bad]
-        bad = bad[(sub[:, 1:] == sub[:, :-1]).any(axis=1)]
+        bad = bad[_rows_with_repeats(sub)]
     wr = rng_for(seed, _S_AW)
     if weight_law == "uniform":
         w = 1.0 - wr.random(size=(n_u, m))          # uniform(0, 1]
