@@ -11,8 +11,8 @@ namespace ahpp {
 constexpr int kQ1Threads = 1024;
 constexpr int kQ1Warps = kQ1Threads / 32;
 constexpr int kQ1Blocks = 1;
-// Default lanes per short row (the fastest on the medium graph: 34.5 ms a
-// query against 35.0 / 40.7 / 42.4 / 69.8 for 4 / 1 / 8 / 32 lanes).
+// Default lanes per short row (the fastest on the medium graph: 33.7 ms a
+// query against 39.7 / 40.0 / 70.4 for 1 / 8 / 32 lanes, autotuner timings).
 constexpr uint32_t kQ1VecWidthDefault = 2;
 
 struct Q1State {
