@@ -374,3 +374,34 @@ def test_power_iteration_invalid(ahpp, tiny):
         with pytest.raises(ahpp.AhppError) as e:
             G.power_iteration(q, T)
         assert e.value.code == ahpp.AHPP_EINVAL
+
+
+def test_source_below_threshold_pushes_nothing(ahpp, tiny):
+    """The degenerate case of Algorithms 3 and 4: with eps / lambda above the
+    source's unit residue no node is ever selected, so the result is the
+    zero vector after 0 rounds (the oracle agrees), and its top-k are the k
+    smallest caller ids at score 0 (score descending, id ascending).  Single
+    query, a batched launch whose other lane is an ordinary query, and the
+    server."""
+    G, og, lam, q, q2 = tiny["G"], tiny["og"], tiny["lam"], tiny["qs"][0], tiny["qs"][1]
+    big = 2.0 * lam                                # eps_f = 2 > r(q) = 1
+    ref = og.push("asrp", ALPHA, BETA, q, big, lam=lam)
+    assert ref.stats["rounds"] == 0 and not ref.pi.any()
+    pi, st, rc = G.query_dense(q, big)
+    assert rc == 0 and st["status"] == 0 and st["rounds"] == 0 and not pi.any()
+    top = G.query(q, big, 5)
+    assert top.nodes.tolist() == [0, 1, 2, 3, 4] and not top.scores.any()
+    dense, stats, rc = G.query_batch_dense([q, q2], [big, 1e-6])
+    assert rc == 0 and stats[0]["rounds"] == 0 and not dense[0].any()
+    ref2 = og.push("asrp", ALPHA, BETA, q2, 1e-6, lam=lam)
+    assert np.abs(dense[1].astype(np.float64) - ref2.pi).max() <= TOL
+    res = G.query_batch([q, q2], [big, 1e-6], 5)
+    assert res[0].nodes.tolist() == [0, 1, 2, 3, 4] and not res[0].scores.any()
+    srv = ahpp.Server(G, max_slots=32, rounds_per_step=2)
+    try:
+        t = [srv.submit(q, big, 5), srv.submit(q2, 1e-6, 5)]
+        r0, r1 = srv.wait(t[0], 5), srv.wait(t[1], 5)
+    finally:
+        srv.stop()
+    assert r0.stats["rounds"] == 0 and r0.nodes.tolist() == [0, 1, 2, 3, 4] and not r0.scores.any()
+    assert r1.nodes.tolist() == res[1].nodes.tolist()
